@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the LRE hot path (steps i+ii: counts -> theta -> rho).
+
+Default workload (the configuration the headline metric is quoted on):
+n = 14 qubits, GHZ state mixed with 5% white noise, 3^14 = 4,782,969 Pauli
+bases x 2^14 outcomes, 1000 shots per basis, int16 counts (156.7 GB) drawn
+on the device by the counter-based generator in synth/ before timing.
+A step is one lre_estimate call (count ingest, parity transform + fold +
+1/(N 3^k) weight, Pauli-to-matrix assembly of the complex64 rho).  The
+projection (step iii) is timed separately with --project.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle (the
+paper's zero-dropped direct sum) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "n14": dict(n=14, state="ghz", p=0.05, shots=1000, kind="i16", seed=14,
+                desc="n=14 GHZ+5% white noise, 4782969 bases x 16384 outcomes, 1000 shots/basis, "
+                     "int16 counts generated on device"),
+    "n12": dict(n=12, state="product", shrink=0.95, shots=4096, kind="i32", seed=12,
+                desc="n=12 product of Haar single-qubit states, 5% depolarising, 531441 bases x "
+                     "4096 outcomes, 4096 shots/basis, int32 counts"),
+    "n10": dict(n=10, state="ghz", p=0.10, shots=1000, kind="i32", seed=10,
+                desc="n=10 GHZ+10% white noise, 59049 bases x 1024 outcomes, 1000 shots/basis, int32"),
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_digest(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from profiles/traffic.txt when the kernel's
+    sources are unchanged since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    digest = source_digest(["paper_1602_08604_gb300/csrc/fold.cu"])
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
+                return float(parts[2]) if parts[3] == digest else None
+    return None
+
+
+def make_counts(torch, wl, device):
+    from synth import gen
+    n = wl["n"]
+    dt = torch.int16 if wl["kind"] == "i16" else torch.int32
+    counts = torch.empty((3 ** n, 2 ** n), dtype=dt, device=device)
+    if wl["state"] == "ghz":
+        gen.gen_ghz(n, wl["p"], wl["shots"], wl["seed"], counts)
+    elif wl["state"] == "product":
+        from synth import states as st
+        bloch = st.haar_bloch_vectors(n, seed=wl["seed"], shrink=wl["shrink"])
+        gen.gen_product(bloch, wl["shots"], wl["seed"], counts)
+    torch.cuda.synchronize()
+    return counts
+
+
+def cpu_rows(wl, bases):
+    import numpy as np
+    from synth import counts as sc
+    n = wl["n"]
+    dt = np.int16 if wl["kind"] == "i16" else np.int32
+    if wl["state"] == "ghz":
+        return sc.sample_ghz(n, wl["p"], wl["shots"], wl["seed"], bases=bases, dtype=dt)
+    from synth import states as st
+    bloch = st.haar_bloch_vectors(n, seed=wl["seed"], shrink=wl["shrink"])
+    return sc.sample_product(bloch, wl["shots"], wl["seed"], bases=bases, dtype=dt)
+
+
+def oracle_sample(wl, seconds_target=15.0, max_bases=None):
+    """Time the CPU oracle's direct sum (steps i, per basis) on the first
+    bases of the workload; returns (bases/s, bases, seconds, threads)."""
+    import numpy as np
+    from oracle import direct
+    n = wl["n"]
+    threads = direct.set_threads(0)
+    P = 4 ** n
+    S = np.zeros(P, np.int64)
+    diag = np.zeros(P, np.int64)
+    probe = 16
+    rows = cpu_rows(wl, np.arange(probe))
+    t0 = time.perf_counter()
+    direct.parity_sums(rows, n, b0=0, b1=probe, S=S, diag=diag)
+    dt = time.perf_counter() - t0
+    k = max(probe, int(seconds_target / max(dt / probe, 1e-9)))
+    k = min(k, 3 ** n) if max_bases is None else min(k, max_bases, 3 ** n)
+    rows = cpu_rows(wl, np.arange(probe, probe + k))
+    t0 = time.perf_counter()
+    direct.parity_sums(rows, n, b0=probe, b1=probe + k, S=S, diag=diag)
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt, threads
+
+
+def spot_check(torch, wl, theta, rho, n_entries=96, n_rho=32):
+    """Bit-exact theta on sampled Pauli strings and rho on sampled elements
+    against the oracle (counts regenerated on the CPU)."""
+    import numpy as np
+    from oracle import direct
+    n = wl["n"]
+    rng = np.random.default_rng(2024)
+    idx = []
+    for _ in range(n_entries):
+        k = int(rng.integers(0, min(n, 4) + 1))         # biased to few identity letters
+        dig = rng.integers(1, 4, size=n)
+        dig[rng.choice(n, size=k, replace=False)] = 0
+        idx.append(int(sum(int(dig[q]) << (2 * (n - 1 - q)) for q in range(n))))
+    idx[0] = 0
+    want = direct.estimate_entries(n, idx, lambda b: cpu_rows(wl, b), wl["shots"])
+    got = theta[torch.tensor(idx, device=theta.device)].cpu().numpy()
+    ok_theta = bool(np.array_equal(got, want))
+    t_host = theta.cpu().numpy()
+    d = 2 ** n
+    r = rng.integers(0, d, n_rho)
+    c = rng.integers(0, d, n_rho)
+    ref = direct.mu_elements(t_host, n, r, c)
+    gr = rho[torch.from_numpy(r).to(rho.device), torch.from_numpy(c).to(rho.device)].cpu().numpy()
+    err = float(np.max(np.abs(gr - ref)) / max(np.max(np.abs(ref)), 1e-30))
+    return {"theta_entries": len(idx), "theta_bit_exact": ok_theta,
+            "rho_entries": n_rho, "rho_max_rel_err": err}
+
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1602_08604_gb300 import lre
+    n = wl["n"]
+    counts = make_counts(torch, wl, device)
+    theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
+    rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
+    ctx = lre.lre_create(local)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        lre.lre_estimate(ctx, counts, wl["shots"], n, theta, rho, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    lre.lre_sync(ctx, stream)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = lre.lre_launch_count(ctx)
+    lre.lre_profile(ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    lre.lre_sync(ctx, stream)
+    recs = lre.lre_profile_records(ctx)
+    lre.lre_profile(ctx, False)
+    launches = lre.lre_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms = total_ms / args.steps
+    B = 3 ** n
+    value = B * world / (ms / 1000.0)
+
+    per = {}
+    for name, t in recs:
+        a = per.setdefault(name, [0.0, 0])
+        a[0] += t
+        a[1] += 1
+    top = max(per.items(), key=lambda kv: kv[1][0])
+    top_name, (top_ms, top_n) = top
+    avg_ms = top_ms / top_n
+    count_bytes = (2 if wl["kind"] == "i16" else 4)
+    alg_bytes = {  # algorithmic bytes per launch of each kernel
+        "fold_first6": B * (2 ** n) * count_bytes,
+    }.get(top_name)
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if alg_bytes else None
+    roofline = {"bound": "hbm", "kernel": top_name,
+                "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": recorded_traffic(top_name, args.workload),
+                "kernel_ms": round(avg_ms, 3),
+                "alg_bytes_per_launch": alg_bytes}
+    step_alg = B * (2 ** n) * count_bytes + 8 * 4 ** n * 2 + 8 * 4 ** n
+    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in per.items()}
+    check = spot_check(torch, wl, theta, rho) if args.check and rank == 0 else None
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            bps, k, dt, thr = oracle_sample(wl, seconds_target=args.cpu_seconds)
+            cpu = {"value": round(bps, 3), "unit": "Pauli bases/s", "cores": thr, "kind": "oracle",
+                   "sample": f"oracle direct zero-dropped sum over the first {k} bases of the same "
+                             f"n={n} workload (counts regenerated on the CPU), {dt:.1f} s"}
+        out = {
+            "metric": "Pauli bases/sec and end-to-end LRE seconds at n=14; fraction of HBM roofline",
+            "value": round(value, 1), "unit": "Pauli bases/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "lre_seconds": round(ms / 1000, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "shots_per_basis": wl["shots"],
+                       "counts_dtype": wl["kind"], "step": "lre_estimate: counts -> theta (FP64) -> rho (c64)",
+                       "l2": "inputs larger than L2 (no flush needed)",
+                       "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+            "kernels": kernels,
+            "step_alg_bytes": step_alg,
+            "step_alg_gbs": round(step_alg / (ms / 1e3) / 1e9, 1),
+        }
+        if check:
+            out["parity"] = check
+    lre.lre_destroy(ctx)
+    return out
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    vals = []
+    for i in range(args.warmup + args.steps):
+        bps, k, dt, thr = oracle_sample(wl, seconds_target=args.ref_step_seconds)
+        if i >= args.warmup:
+            vals.append((bps, k, dt))
+    bps = sum(v[0] for v in vals) / len(vals)
+    ms = sum(v[2] for v in vals) / len(vals) * 1000
+    sample = (f"oracle direct zero-dropped sum over {vals[0][1]} bases of the n={wl['n']} workload "
+              f"per step")
+    return {"impl": "reference", "metric": "Pauli bases/sec and end-to-end LRE seconds at n=14; fraction of HBM roofline",
+            "value": round(bps, 3), "unit": "Pauli bases/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": wl["desc"]},
+            "cpu_baseline": {"value": round(bps, 3), "unit": "Pauli bases/s", "cores": thr,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(bps, 3), "unit": "Pauli bases/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="n14", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    out = run_reference(args, wl) if args.impl == "reference" else run_ours(args, wl)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

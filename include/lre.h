@@ -1,0 +1,167 @@
+/*
+ * lre.h -- C ABI of the GB300 linear-regression-estimation (LRE) hot path for
+ * full quantum state tomography under Pauli measurements
+ * (arXiv:1602.08604, "Full reconstruction of a 14-qubit state within four
+ * hours").
+ *
+ * The three steps of the paper (Sec. II):
+ *   step (i)   measured frequencies of the 6^n Pauli eigenprojectors ->
+ *              least-squares coefficient vector theta (Eq. 3, Sec. III);
+ *   step (ii)  theta -> Hermitian unit-trace mu = sum_i theta_i Omega_i
+ *              (Eq. 4);
+ *   step (iii) mu -> the closest physical density matrix (Sec. II, the
+ *              Smolin-Gambetta-Smith algorithm).
+ *
+ * Conventions (every index has qubit 1 as its most significant digit):
+ *   basis   b = sum_q a_q 3^(n-q),  a_q in {0:X, 1:Y, 2:Z}      (3^n bases)
+ *   outcome o = sum_q o_q 2^(n-q),  o_q = 0: the +1 eigenvector (2^n outcomes)
+ *   Pauli   i = sum_q p_q 4^(n-q),  p_q in {0:I, 1:X, 2:Y, 3:Z} (Eq. 5 order)
+ *   counts  [3^n][2^n] row-major (int32 or int16), counts[b][o] = number of
+ *           shots of basis b that gave outcome o.
+ *   theta   FP64 [4^n] in Eq. (5) order, holding the Pauli expectation
+ *           estimates t_i = 2^{n/2} theta_i^{LS}; theta[0] = 1 exactly.
+ *           (The paper's orthonormal-basis coefficient is 2^{-n/2} t_i.)
+ *   rho     complex64 [2^n][2^n] row-major, rho = (1/2^n) sum_i t_i P_i.
+ *
+ * Memory: every pointer argument named "device" must be CUDA device memory
+ * on the context's device; the caller owns it, the library only borrows it
+ * for the call.  The context owns its workspace (device memory grown on
+ * demand, capped by lre_set_workspace_limit) and its library handles.
+ *
+ * Asynchrony: compute calls enqueue work on `stream` and return.  Argument
+ * errors are returned synchronously and nothing is enqueued.  Errors found
+ * by kernels (a count total that disagrees with the stated shots, a shot
+ * record outside [0, 2^n)) are latched in the context and returned by
+ * lre_sync().  No C++ exception crosses this ABI.
+ *
+ * Supported sizes: 1 <= n <= 14 for every call (n <= 12 for lre_project on
+ * hosts without enough device memory for three d x d complex128 matrices).
+ */
+#ifndef LRE_H
+#define LRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRE_OK = 0,
+  LRE_ERR_INVALID_ARG = 1,    /* bad pointer, size, kind or shot count        */
+  LRE_ERR_UNSUPPORTED = 2,    /* n outside the supported range                */
+  LRE_ERR_SHOTS_MISMATCH = 3, /* counts do not add up to the stated shots     */
+  LRE_ERR_OOM = 4,            /* workspace above the limit or cudaMalloc fail */
+  LRE_ERR_CUDA = 5,           /* a CUDA runtime / library call failed         */
+  LRE_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up           */
+  LRE_ERR_EIG_FAILED = 7      /* the Hermitian eigensolver reported failure   */
+} lre_status;
+
+typedef enum {
+  LRE_COUNTS_I32 = 0, /* int32 counts */
+  LRE_COUNTS_I16 = 1  /* int16 counts (each count <= 32767)                   */
+} lre_count_kind;
+
+typedef struct {
+  float re, im;
+} lre_c64;
+
+typedef struct CUstream_st *lre_stream; /* the same handle as cudaStream_t   */
+typedef struct lre_ctx lre_ctx;
+
+/* Create a context on CUDA device `device` (creates its cuSOLVER/cuBLAS
+ * handles lazily).  *out receives the context. */
+lre_status lre_create(lre_ctx **out, int device);
+
+/* Free the context, its workspace and handles.  NULL is allowed. */
+void lre_destroy(lre_ctx *ctx);
+
+/* Cap the workspace the context may hold (bytes; 0 = no cap).  A call whose
+ * plan needs more returns LRE_ERR_OOM without enqueuing anything. */
+lre_status lre_set_workspace_limit(lre_ctx *ctx, size_t bytes);
+
+/* Workspace bytes lre_estimate needs for this n and count kind
+ * (per_basis_shots != 0 for the per-basis FP64 weighting). */
+lre_status lre_workspace_size(lre_ctx *ctx, int n, lre_count_kind kind, int per_basis_shots,
+                              size_t *bytes);
+
+/* Step (i) without the weight: exact integer parity sums
+ *   S[i] = sum over bases b compatible with Pauli string i of
+ *          sum_o counts[b][o] * (-1)^{popcount(o & support(i))},
+ * where b is compatible with i when i's non-identity letters equal b's axes
+ * (Sec. III: the 2^n nonzeros of each Gamma^(j) and the shared 2^n x 2^n
+ * nonzero matrix of each basis group).  counts: device [3^n][2^n];
+ * row_total_bound: an upper bound on every row's sum of counts (the shots
+ * per basis), or 0 if unknown (then all partial sums are int64); S: device
+ * int64 [4^n], overwritten.  Bit-exact whenever the bound holds. */
+lre_status lre_parity_sums(lre_ctx *ctx, const void *counts, lre_count_kind kind, int n,
+                           int64_t row_total_bound, int64_t *S, lre_stream stream);
+
+/* Steps (i)+(ii): Eq. (3) with the diagonal X^T X of Sec. III, i.e.
+ *   theta[i] = S[i] / (N * 3^k(i))           (uniform shots N)
+ *   theta[i] = (sum_b Shat_b[i] / N_b) / 3^k (per-basis shots N_b)
+ * with k(i) the number of identity letters of i, then, when rho != NULL,
+ * Eq. (4): rho = (1/2^n) sum_i theta[i] P_i.
+ * counts: device [3^n][2^n]; shots: device int64 [3^n] per-basis totals, or
+ * NULL to use shots_uniform (> 0) for every basis; theta: device FP64 [4^n];
+ * rho: device complex64 [2^n][2^n] or NULL.  With uniform shots theta is the
+ * correctly rounded quotient of two exact integers.  When the counts' grand
+ * total differs from shots_uniform * 3^n, LRE_ERR_SHOTS_MISMATCH is latched
+ * (returned by lre_sync). */
+lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, const int64_t *shots,
+                        int64_t shots_uniform, int n, double *theta, lre_c64 *rho,
+                        lre_stream stream);
+
+/* Step (ii) alone, Eq. (4): rho = (1/2^n) sum_i theta[i] P_i, computed in
+ * FP64 and rounded once to complex64.  theta: device FP64 [4^n];
+ * rho: device complex64 [2^n][2^n]. */
+lre_status lre_assemble(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, lre_stream stream);
+
+/* Step (iii): rho_out = argmin over density matrices sigma of
+ * ||sigma - rho_in||_F (Sec. II, Smolin et al.): FP64 Hermitian
+ * eigendecomposition of rho_in (promoted to complex128), the eigenvalue
+ * correction onto the probability simplex, and the reconstruction in FP64
+ * rounded once to complex64.  rho_in, rho_out: device complex64
+ * [2^n][2^n] (may alias); eig_mu, eig_rho: device FP64 [2^n] or NULL,
+ * receiving the spectra of rho_in and rho_out in decreasing order.  The call
+ * synchronises `stream` once (to size the reconstruction). */
+lre_status lre_project(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,
+                       double *eig_mu, double *eig_rho, lre_stream stream);
+
+/* Count ingest from shot records: counts[b][o] = #{s : records[b][s] == o}.
+ * records: device uint16 [num_bases][shots_per_basis]; counts: device
+ * [num_bases][2^n] of `kind`, overwritten.  A record >= 2^n latches
+ * LRE_ERR_INVALID_ARG. */
+lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,
+                         int64_t shots_per_basis, int n, void *counts, lre_count_kind kind,
+                         lre_stream stream);
+
+/* Synchronise `stream` and return (and clear) the first error latched by a
+ * kernel since the last lre_sync. */
+lre_status lre_sync(lre_ctx *ctx, lre_stream stream);
+
+/* Static text for a status code. */
+const char *lre_status_string(lre_status s);
+
+/* Text of the last CUDA / library error seen by this context ("" if none). */
+const char *lre_last_error(lre_ctx *ctx);
+
+/* Tracing: when enabled, every kernel launch (and every cuSOLVER / cuBLAS
+ * call) made by the context is bracketed by a pair of CUDA events on its
+ * stream.  lre_profile(ctx, 1) clears the record and starts recording;
+ * lre_profile(ctx, 0) stops.  After the stream is synchronised,
+ * lre_profile_get(ctx, i, &name, &ms) returns the i-th record (0 <=
+ * i < lre_profile_count(ctx)): a static name and its device time in ms. */
+lre_status lre_profile(lre_ctx *ctx, int enable);
+int lre_profile_count(lre_ctx *ctx);
+lre_status lre_profile_get(lre_ctx *ctx, int i, const char **name, float *ms);
+
+/* Number of this library's own kernels launched by the context so far
+ * (library calls such as the eigensolver are not counted). */
+uint64_t lre_launch_count(lre_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRE_H */

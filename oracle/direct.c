@@ -62,7 +62,7 @@ static int64_t location_index(int n, int64_t b, uint32_t m) {
 /* The shared 2^n x 2^n nonzero matrix: entry [m][o] is the product over
  * qubits of the single-qubit Gamma values (times 2^{n/2}): +1 on identity
  * sites, (-1)^{o_q} on measured sites. */
-static int8_t *nonzero_matrix(int n) {
+static int8_t *nonzero_matrix_build(int n) {
   size_t d = (size_t)1 << n;
   int8_t *H = (int8_t *)malloc(d * d);
   if (!H) return NULL;
@@ -73,6 +73,24 @@ static int8_t *nonzero_matrix(int n) {
         if (((m >> j) & 1u) && ((o >> j) & 1u)) v = -v;
       H[m * d + o] = (int8_t)v;
     }
+  return H;
+}
+
+/* The nonzero matrix is the same for every group (Sec. III): build it once
+ * per n and keep it. */
+static int8_t *H_cache = NULL;
+static int H_cache_n = -1;
+static int8_t *nonzero_matrix(int n) {
+  int8_t *H = NULL;
+#pragma omp critical(oracle_nonzero_matrix)
+  {
+    if (H_cache_n != n) {
+      free(H_cache);
+      H_cache = nonzero_matrix_build(n);
+      H_cache_n = H_cache ? n : -1;
+    }
+    H = H_cache;
+  }
   return H;
 }
 
@@ -105,7 +123,6 @@ int oracle_direct_sums(int n, const void *counts, int kind, int64_t b0, int64_t 
       }
     }
   }
-  free(H);
   return 0;
 }
 
@@ -131,7 +148,6 @@ int oracle_direct_weighted(int n, const void *counts, int kind, const int64_t *s
       }
     }
   }
-  free(H);
   return 0;
 }
 
@@ -212,5 +228,41 @@ void oracle_direct_mu(int n, const double *t, double *mu_re, double *mu_im) {
       mu_re[r * d + c] = sr * scale;
       mu_im[r * d + c] = si * scale;
     }
+  }
+}
+
+/* Spot values of step (i) for chosen Pauli indices (large-n parity checks):
+ * S_i = sum over the 3^k groups whose locations include i of the nonzero-
+ * matrix row of i times the group's counts.  `row_of(b)` rows are supplied by
+ * the caller as `counts` with a row table: rows[k] is the row (in counts) of
+ * the k-th compatible group of entry e, enumerated in increasing basis index.
+ * Here the caller passes, per entry, its compatible groups' counts
+ * contiguously: counts_e = counts + offsets[e] * 2^n, 3^k rows.  kind: 0 int32,
+ * 1 int16. */
+void oracle_direct_entries(int n, const void *counts, int kind, const int64_t *indices,
+                           const int64_t *offsets, int64_t count, int64_t *S) {
+  const int64_t d = (int64_t)1 << n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t e = 0; e < count; ++e) {
+    const int64_t i = indices[e];
+    uint32_t m = 0;
+    int k = 0;
+    for (int j = 0; j < n; ++j) {
+      if (((i >> (2 * j)) & 3) != 0) m |= 1u << j;
+      else ++k;
+    }
+    int64_t groups = 1;
+    for (int j = 0; j < k; ++j) groups *= 3;
+    int64_t acc = 0;
+    for (int64_t g = 0; g < groups; ++g) {
+      const size_t row = (size_t)(offsets[e] + g) * (size_t)d;
+      for (int64_t o = 0; o < d; ++o) {
+        int v = 1;
+        for (int j = 0; j < n; ++j)
+          if (((m >> j) & 1u) && ((o >> j) & 1)) v = -v;
+        acc += (int64_t)v * count_at(counts, kind, row + (size_t)o);
+      }
+    }
+    S[e] = acc;
   }
 }

@@ -112,3 +112,49 @@ def mu_elements(t, n, rows, cols):
     im = np.empty(len(rows), np.float64)
     lib().oracle_direct_mu_elements(n, _ptr(t), _ptr(rows), _ptr(cols), len(rows), _ptr(re), _ptr(im))
     return re + 1j * im
+
+
+def compatible_bases(i, n):
+    """Basis indices (increasing) of the groups whose locations include Pauli
+    index i: the non-identity letters fix those digits, identity sites range
+    over X, Y, Z."""
+    digits = [(i >> (2 * (n - 1 - q))) & 3 for q in range(n)]  # qubit 1 first
+    bases = [0]
+    for p in digits:
+        if p == 0:
+            bases = [3 * b + a for b in bases for a in range(3)]
+        else:
+            bases = [3 * b + (p - 1) for b in bases]
+    return bases
+
+
+def parity_sum_entries(n, indices, rows_for):
+    """S_i for selected Pauli indices.  rows_for(bases) must return the counts
+    rows (len(bases), 2^n) of those bases (int32 or int16)."""
+    L = lib()
+    if not hasattr(L, "_entries_set"):
+        L.oracle_direct_entries.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L._entries_set = True
+    idx = np.asarray(indices, dtype=np.int64)
+    all_bases, offs = [], []
+    for i in idx:
+        offs.append(len(all_bases))
+        all_bases.extend(compatible_bases(int(i), n))
+    rows = np.ascontiguousarray(rows_for(np.array(all_bases, dtype=np.int64)))
+    offs = np.ascontiguousarray(np.array(offs, dtype=np.int64))
+    S = np.empty(len(idx), np.int64)
+    L.oracle_direct_entries(n, _ptr(rows), _kind(rows), _ptr(np.ascontiguousarray(idx)), _ptr(offs),
+                            len(idx), _ptr(S))
+    return S
+
+
+def identity_letters(i, n):
+    return sum(((int(i) >> (2 * q)) & 3) == 0 for q in range(n))
+
+
+def estimate_entries(n, indices, rows_for, shots):
+    """t_i = S_i / (N 3^k) for selected indices (uniform shots)."""
+    S = parity_sum_entries(n, indices, rows_for)
+    k = np.array([identity_letters(i, n) for i in indices])
+    return S.astype(np.float64) / (float(shots) * (3.0 ** k))

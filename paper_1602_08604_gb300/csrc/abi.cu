@@ -1,0 +1,303 @@
+// C ABI of liblre (declarations and documentation in include/lre.h):
+// argument validation, the context and its workspace, and the count-ingest
+// (shot-record histogram) kernel.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <new>
+#include <string>
+
+#include "lre_internal.cuh"
+
+namespace lre {
+
+lre_status cuda_fail(lre_ctx *ctx, cudaError_t e, const char *where) {
+  if (ctx) ctx->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? LRE_ERR_OOM : LRE_ERR_CUDA;
+}
+
+lre_status ensure_workspace(lre_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return LRE_OK;
+  if (ctx->ws_limit != 0 && bytes > ctx->ws_limit) {
+    ctx->last_error = "workspace of " + std::to_string(bytes) + " bytes exceeds the limit of " +
+                      std::to_string(ctx->ws_limit);
+    return LRE_ERR_OOM;
+  }
+  if (ctx->ws) {
+    cudaError_t e = cudaFree(ctx->ws);  // implicit device synchronisation
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(workspace)");
+  }
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) {
+    ctx->ws = nullptr;
+    cudaGetLastError();
+    return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+  }
+  ctx->ws_bytes = bytes;
+  return LRE_OK;
+}
+
+Launch::Launch(lre_ctx *ctx, const char *name, cudaStream_t s, int own) : ctx_(ctx), s_(s) {
+  ctx->launches += (uint64_t)own;
+  if (!ctx->prof) return;
+  if (ctx->prof_used == ctx->prof_pool.size()) {
+    lre_prof_entry e{name, nullptr, nullptr};
+    if (cudaEventCreate(&e.start) != cudaSuccess || cudaEventCreate(&e.stop) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    ctx->prof_pool.push_back(e);
+  }
+  idx_ = (long)ctx->prof_used++;
+  ctx->prof_pool[idx_].name = name;
+  cudaEventRecord(ctx->prof_pool[idx_].start, s);
+}
+
+Launch::~Launch() {
+  if (idx_ >= 0) cudaEventRecord(ctx_->prof_pool[idx_].stop, s_);
+}
+
+namespace {
+
+// One CTA per basis (grid-stride): a shared-memory histogram of the basis'
+// shot records, then one coalesced write of its 2^n counts.
+template <typename OutT>
+__global__ void histogram_kernel(const uint16_t *__restrict__ rec, int64_t B, int64_t S, int n,
+                                 OutT *__restrict__ counts, int *status) {
+  extern __shared__ int32_t h[];
+  const int d = 1 << n;
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    for (int o = threadIdx.x; o < d; o += blockDim.x) h[o] = 0;
+    __syncthreads();
+    const uint16_t *r = rec + b * S;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+      const int o = r[s];
+      if (o < d) atomicAdd(&h[o], 1);
+      else latch(status, LRE_ERR_INVALID_ARG);
+    }
+    __syncthreads();
+    OutT *c = counts + b * (int64_t)d;
+    for (int o = threadIdx.x; o < d; o += blockDim.x) c[o] = (OutT)h[o];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+lre_status histogram_run(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,
+                         int64_t shots_per_basis, int n, void *counts, lre_count_kind kind,
+                         cudaStream_t s) {
+  const size_t smem = sizeof(int32_t) << n;
+  int grid = ctx->num_sms * 4;
+  if (grid > num_bases) grid = (int)num_bases;
+  Launch L(ctx, "histogram", s);
+  if (kind == LRE_COUNTS_I16) {
+    cudaFuncSetAttribute(histogram_kernel<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    histogram_kernel<int16_t><<<grid, 512, smem, s>>>(records, num_bases, shots_per_basis, n,
+                                                      static_cast<int16_t *>(counts), ctx->d_status);
+  } else {
+    cudaFuncSetAttribute(histogram_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    histogram_kernel<int32_t><<<grid, 512, smem, s>>>(records, num_bases, shots_per_basis, n,
+                                                      static_cast<int32_t *>(counts), ctx->d_status);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "histogram launch");
+}
+
+}  // namespace lre
+
+using namespace lre;
+
+namespace {
+constexpr int kMaxN = 14;
+
+lre_status check_ctx(lre_ctx *ctx) { return ctx ? LRE_OK : LRE_ERR_INVALID_ARG; }
+
+lre_status check_n(int n) {
+  if (n < 1) return LRE_ERR_INVALID_ARG;
+  if (n > kMaxN) return LRE_ERR_UNSUPPORTED;
+  return LRE_OK;
+}
+
+lre_status set_device(lre_ctx *ctx) {
+  cudaError_t e = cudaSetDevice(ctx->device);
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "cudaSetDevice");
+}
+}  // namespace
+
+extern "C" {
+
+lre_status lre_create(lre_ctx **out, int device) {
+  if (!out) return LRE_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return LRE_ERR_INVALID_ARG;
+  }
+  lre_ctx *ctx = new (std::nothrow) lre_ctx();
+  if (!ctx) return LRE_ERR_OOM;
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    lre_status st = cuda_fail(ctx, e, "lre_create");
+    lre_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return LRE_OK;
+}
+
+void lre_destroy(lre_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->solver) cusolverDnDestroy(reinterpret_cast<cusolverDnHandle_t>(ctx->solver));
+  if (ctx->blas) cublasDestroy(reinterpret_cast<cublasHandle_t>(ctx->blas));
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  for (auto &e : ctx->prof_pool) {
+    cudaEventDestroy(e.start);
+    cudaEventDestroy(e.stop);
+  }
+  delete ctx;
+}
+
+lre_status lre_set_workspace_limit(lre_ctx *ctx, size_t bytes) {
+  if (check_ctx(ctx) != LRE_OK) return LRE_ERR_INVALID_ARG;
+  ctx->ws_limit = bytes;
+  return LRE_OK;
+}
+
+lre_status lre_workspace_size(lre_ctx *ctx, int n, lre_count_kind kind, int per_basis_shots,
+                              size_t *bytes) {
+  if (check_ctx(ctx) != LRE_OK || !bytes) return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
+  const size_t f = fold_workspace_bytes(n, kind, per_basis_shots != 0, per_basis_shots ? 0 : 1);
+  const size_t a = assemble_workspace_bytes(n);
+  *bytes = f > a ? f : a;
+  return LRE_OK;
+}
+
+lre_status lre_parity_sums(lre_ctx *ctx, const void *counts, lre_count_kind kind, int n,
+                           int64_t row_total_bound, int64_t *S, lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK || !counts || !S || row_total_bound < 0) return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != LRE_OK) return st;
+  // Without a bound every partial sum is int64.
+  const size_t need = fold_workspace_bytes(n, kind, false, row_total_bound);
+  if ((st = ensure_workspace(ctx, need)) != LRE_OK) return st;
+  FoldArgs a{counts, kind, n, nullptr, row_total_bound, nullptr, S};
+  return fold_run(ctx, a, ctx->ws, ctx->ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, const int64_t *shots,
+                        int64_t shots_uniform, int n, double *theta, lre_c64 *rho,
+                        lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK || !counts || !theta) return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
+  if (!shots && shots_uniform <= 0) return LRE_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != LRE_OK) return st;
+  const size_t f = fold_workspace_bytes(n, kind, shots != nullptr, shots ? 0 : shots_uniform);
+  const size_t a = rho ? assemble_workspace_bytes(n) : 0;
+  if ((st = ensure_workspace(ctx, f > a ? f : a)) != LRE_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FoldArgs fa{counts, kind, n, shots, shots_uniform, theta, nullptr};
+  if ((st = fold_run(ctx, fa, ctx->ws, ctx->ws_bytes, s)) != LRE_OK) return st;
+  if (rho) st = assemble_run(ctx, theta, n, rho, ctx->ws, s);
+  return st;
+}
+
+lre_status lre_assemble(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK || !theta || !rho) return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if ((st = set_device(ctx)) != LRE_OK) return st;
+  if ((st = ensure_workspace(ctx, assemble_workspace_bytes(n))) != LRE_OK) return st;
+  return assemble_run(ctx, theta, n, rho, ctx->ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lre_status lre_project(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,
+                       double *eig_mu, double *eig_rho, lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK || !rho_in || !rho_out) return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if ((st = set_device(ctx)) != LRE_OK) return st;
+  return project_run(ctx, rho_in, n, rho_out, eig_mu, eig_rho, reinterpret_cast<cudaStream_t>(stream));
+}
+
+lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,
+                         int64_t shots_per_basis, int n, void *counts, lre_count_kind kind,
+                         lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK || !records || !counts || num_bases <= 0 || shots_per_basis <= 0)
+    return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
+  if (kind == LRE_COUNTS_I16 && shots_per_basis > 32767) return LRE_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != LRE_OK) return st;
+  return histogram_run(ctx, records, num_bases, shots_per_basis, n, counts, kind,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+lre_status lre_sync(lre_ctx *ctx, lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK) return LRE_ERR_INVALID_ARG;
+  lre_status st = set_device(ctx);
+  if (st != LRE_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int code = 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&code, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && code != 0) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "lre_sync");
+  return static_cast<lre_status>(code);
+}
+
+const char *lre_status_string(lre_status s) {
+  switch (s) {
+    case LRE_OK: return "ok";
+    case LRE_ERR_INVALID_ARG: return "invalid argument";
+    case LRE_ERR_UNSUPPORTED: return "unsupported size";
+    case LRE_ERR_SHOTS_MISMATCH: return "counts do not add up to the stated shots";
+    case LRE_ERR_OOM: return "out of device memory / workspace limit";
+    case LRE_ERR_CUDA: return "CUDA error";
+    case LRE_ERR_TIMEOUT: return "bounded device wait timed out";
+    case LRE_ERR_EIG_FAILED: return "eigensolver failed";
+  }
+  return "unknown status";
+}
+
+const char *lre_last_error(lre_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+lre_status lre_profile(lre_ctx *ctx, int enable) {
+  if (check_ctx(ctx) != LRE_OK) return LRE_ERR_INVALID_ARG;
+  ctx->prof = enable != 0;
+  ctx->prof_used = 0;
+  return LRE_OK;
+}
+
+int lre_profile_count(lre_ctx *ctx) { return ctx ? (int)ctx->prof_used : 0; }
+
+lre_status lre_profile_get(lre_ctx *ctx, int i, const char **name, float *ms) {
+  if (check_ctx(ctx) != LRE_OK || i < 0 || (size_t)i >= ctx->prof_used || !name || !ms)
+    return LRE_ERR_INVALID_ARG;
+  const lre_prof_entry &e = ctx->prof_pool[i];
+  *name = e.name;
+  cudaError_t err = cudaEventElapsedTime(ms, e.start, e.stop);
+  return err == cudaSuccess ? LRE_OK : cuda_fail(ctx, err, "lre_profile_get");
+}
+
+uint64_t lre_launch_count(lre_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

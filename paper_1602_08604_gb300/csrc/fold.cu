@@ -1,0 +1,458 @@
+// Step (i) of the LRE (arXiv:1602.08604 Sec. III, Eq. 3): per-basis counts ->
+// Pauli coefficients, as an atomic-free, mode-blocked Kronecker fold.
+//
+// With the diagonal X^T X of Sec. III the estimate of Pauli string P (support
+// mask m, k identity letters) is
+//     t_P = 1/(N 3^k) * sum_{bases a compatible with P} sum_o c_a(o) (-1)^{o.m}.
+// Per qubit this is one fixed 4x6 integer map T from (axis a_q, outcome o_q)
+// to the Pauli letter p_q:
+//     I <- sum over all six;  X <- c(X,0)-c(X,1);  Y <- c(Y,0)-c(Y,1);  Z <- ...
+// which factors as a 2-point Walsh-Hadamard butterfly over o_q (the parity
+// transform, the paper's "nonzero matrix") followed by a ternary fold over
+// a_q (the paper's "locations": I sums the three axes, X/Y/Z keep one).
+// The whole step is T^{(x)n} applied to the [3^n][2^n] count tensor.  Passes
+// apply it to a block of qubits at a time; every pass reads its input once
+// and writes a tensor 2/3 smaller per contracted qubit.
+//
+// Tensor view before a pass with r qubits still to contract and C = 4^(n-r)
+// coefficient columns already produced:
+//     X[ah][al][oh][ol][c],   al in 3^J, ol in 2^J (the J qubits of the pass)
+// and after it
+//     Y[ah][oh][pl][c],       pl in 4^J,
+// so the last pass leaves theta in the canonical order of Eq. (5).
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "lre_internal.cuh"
+
+namespace lre {
+namespace {
+
+enum { T_I16 = 0, T_I32 = 1, T_I64 = 2, T_F64 = 3 };
+enum { M_STORE = 0, M_FINAL_U = 1, M_FINAL_W = 2, M_PARITY = 3 };
+
+// Pauli-digit index of the pass block: digit q is m_q ? a_q + 1 : 0 (a_q the
+// q-th ternary digit of al, m_q the q-th bit of the parity mask).
+__host__ __device__ constexpr int block_pauli(int al, int m, int J) {
+  int pl = 0, w = 1;
+  for (int q = 0; q < J; ++q) {
+    pl += (((m >> q) & 1) ? (al % 3) + 1 : 0) * w;
+    al /= 3;
+    w *= 4;
+  }
+  return pl;
+}
+
+template <int J, typename V>
+__device__ __forceinline__ void wht(V (&v)[1 << J]) {
+#pragma unroll
+  for (int h = 1; h < (1 << J); h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < (1 << J); ++i) {
+      if ((i & h) == 0) {
+        V a = v[i], b = v[i + h];
+        v[i] = a + b;
+        v[i + h] = a - b;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int identity_letters(uint64_t i, int n) {
+  uint64_t nz = (i | (i >> 1)) & 0x5555555555555555ull;
+  uint64_t mask = (n >= 32) ? ~0ull : ((1ull << (2 * n)) - 1);
+  return n - __popcll(nz & mask);
+}
+
+__device__ __forceinline__ double pow3d(int k) {
+  double r = 1.0;
+  for (int q = 0; q < k; ++q) r *= 3.0;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Two-level first pass over the raw counts: 6 qubits per tile.
+//   tile = (ah, oh): 729 basis rows x 64 consecutive outcomes.
+//   level A (registers): 216 work items (alB in 27, olB in 8); each reads 27
+//     rows x 8 outcomes (one 16 B vector per row for int16) and contracts the
+//     three lowest qubits to 64 partial sums.
+//   level B (shared memory): 64 work items (one per level-A Pauli digit
+//     triple); each contracts the 27 x 8 level-A results over the next three
+//     qubits and writes 64 int32 outputs.
+// ---------------------------------------------------------------------------
+constexpr int P1_THREADS = 256;
+constexpr int P1_ZSTRIDE = 217;  // odd stride: conflict-free level-B reads
+
+template <typename InT>
+__device__ __forceinline__ void load_row8(const InT *p, int32_t (&v)[8]);
+
+template <>
+__device__ __forceinline__ void load_row8<int16_t>(const int16_t *p, int32_t (&v)[8]) {
+  uint4 u = __ldcs(reinterpret_cast<const uint4 *>(p));
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
+    v[2 * k + 1] = ((int32_t)w[k]) >> 16;
+  }
+}
+
+template <>
+__device__ __forceinline__ void load_row8<int32_t>(const int32_t *p, int32_t (&v)[8]) {
+  int4 a = __ldcs(reinterpret_cast<const int4 *>(p));
+  int4 b = __ldcs(reinterpret_cast<const int4 *>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(P1_THREADS, 2)
+    fold_first6(const InT *__restrict__ counts, int32_t *__restrict__ out, int n,
+                int64_t num_tiles) {
+  extern __shared__ int32_t Z[];  // [64][P1_ZSTRIDE]
+  const int t = threadIdx.x;
+  const int64_t d = 1ll << n;
+  const int64_t n_oh = d >> 6;
+  for (int64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+    const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
+    if (t < 216) {
+      const int alB = t >> 3, olB = t & 7;
+      const InT *base = counts + (ah * 729 + alB * 27) * d + oh * 64 + olB * 8;
+      int32_t acc[64];
+#pragma unroll
+      for (int p = 0; p < 64; ++p) acc[p] = 0;
+#pragma unroll
+      for (int alA = 0; alA < 27; ++alA) {
+        int32_t v[8];
+        load_row8<InT>(base + alA * d, v);
+        wht<3>(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[block_pauli(alA, m, 3)] += v[m];
+      }
+#pragma unroll
+      for (int p = 0; p < 64; ++p) Z[p * P1_ZSTRIDE + t] = acc[p];
+    }
+    __syncthreads();
+    if (t < 64) {
+      int32_t acc[64];
+#pragma unroll
+      for (int p = 0; p < 64; ++p) acc[p] = 0;
+      const int32_t *z = Z + t * P1_ZSTRIDE;
+#pragma unroll
+      for (int alB = 0; alB < 27; ++alB) {
+        int32_t v[8];
+#pragma unroll
+        for (int olB = 0; olB < 8; ++olB) v[olB] = z[alB * 8 + olB];
+        wht<3>(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
+      }
+      int32_t *o = out + tile * 4096 + t;
+#pragma unroll
+      for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generic pass: one thread per (ah, oh, c) column, J <= 3 qubits in registers.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Ty;
+template <> struct Ty<int16_t> { static constexpr int id = T_I16; };
+template <> struct Ty<int32_t> { static constexpr int id = T_I32; };
+template <> struct Ty<int64_t> { static constexpr int id = T_I64; };
+template <> struct Ty<double> { static constexpr int id = T_F64; };
+
+struct GenParams {
+  const void *in;
+  void *out;
+  int64_t C;       // columns already produced (4^(n-r))
+  int64_t n_oh;    // 2^(r-J)
+  int64_t items;   // 3^(r-J) * 2^(r-J) * C
+  int r;           // qubits left before this pass
+  int n;
+  const double *wgt;     // 1/N_b per basis (weighted first pass)
+  double shots;          // N (final uniform)
+  int64_t total;         // N * 3^n (final uniform check)
+  int *status;
+};
+
+template <int J, typename InT, typename AccT, int MODE, bool WEIGHT>
+__global__ void __launch_bounds__(256) fold_generic(GenParams P) {
+  constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
+  constexpr int NO = 1 << J;
+  constexpr int NP = 1 << (2 * J);
+  const InT *__restrict__ in = static_cast<const InT *>(P.in);
+  const int64_t row_stride = (1ll << P.r) * P.C;  // al stride
+  for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < P.items;
+       item += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = item % P.C;
+    const int64_t ahoh = item / P.C;
+    const int64_t oh = ahoh % P.n_oh;
+    const int64_t ah = ahoh / P.n_oh;
+    const int64_t base = ((ah * NA) << P.r) * P.C + (oh * NO) * P.C + c;
+    AccT acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = 0;
+#pragma unroll
+    for (int al = 0; al < NA; ++al) {
+      if constexpr (WEIGHT) {
+        int32_t v[NO];
+#pragma unroll
+        for (int ol = 0; ol < NO; ++ol) v[ol] = (int32_t)__ldg(in + base + al * row_stride + ol * P.C);
+        wht<J>(v);
+        const double w = __ldg(P.wgt + ah * NA + al);
+#pragma unroll
+        for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += (double)v[m] * w;
+      } else {
+        AccT v[NO];
+#pragma unroll
+        for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)__ldg(in + base + al * row_stride + ol * P.C);
+        wht<J>(v);
+#pragma unroll
+        for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
+      }
+    }
+    const int64_t obase = ahoh * NP * P.C + c;
+    if constexpr (MODE == M_STORE) {
+      AccT *out = static_cast<AccT *>(P.out);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) out[obase + p * P.C] = acc[p];
+    } else if constexpr (MODE == M_PARITY) {
+      int64_t *out = static_cast<int64_t *>(P.out);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) out[obase + p * P.C] = (int64_t)acc[p];
+    } else {
+      double *out = static_cast<double *>(P.out);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const int64_t i = obase + p * P.C;  // ahoh == 0 in the last pass
+        const int k = identity_letters((uint64_t)i, P.n);
+        if constexpr (MODE == M_FINAL_U) {
+          if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
+          out[i] = (double)acc[p] / (P.shots * pow3d(k));
+        } else {
+          out[i] = (double)acc[p] / pow3d(k);
+        }
+      }
+    }
+  }
+}
+
+using GenKernel = void (*)(GenParams);
+
+template <int J, typename InT, typename AccT, bool WEIGHT>
+GenKernel pick_mode(int mode) {
+  switch (mode) {
+    case M_STORE: return fold_generic<J, InT, AccT, M_STORE, WEIGHT>;
+    case M_FINAL_U:
+      if constexpr (!WEIGHT && !std::is_same<AccT, double>::value)
+        return fold_generic<J, InT, AccT, M_FINAL_U, WEIGHT>;
+      return nullptr;
+    case M_FINAL_W:
+      if constexpr (std::is_same<AccT, double>::value) return fold_generic<J, InT, AccT, M_FINAL_W, WEIGHT>;
+      return nullptr;
+    case M_PARITY:
+      if constexpr (!WEIGHT && !std::is_same<AccT, double>::value)
+        return fold_generic<J, InT, AccT, M_PARITY, WEIGHT>;
+      return nullptr;
+  }
+  return nullptr;
+}
+
+template <int J>
+GenKernel pick_types(int in_t, int acc_t, int mode, bool weight) {
+  if (weight) {  // first pass of the per-basis-weighted path
+    if (in_t == T_I16) return pick_mode<J, int16_t, double, true>(mode);
+    if (in_t == T_I32) return pick_mode<J, int32_t, double, true>(mode);
+    return nullptr;
+  }
+  if (acc_t == T_F64) {
+    if (in_t == T_F64 && J <= 2) return pick_mode<(J <= 2 ? J : 2), double, double, false>(mode);
+    return nullptr;
+  }
+  if (acc_t == T_I32) {
+    if (in_t == T_I16) return pick_mode<J, int16_t, int32_t, false>(mode);
+    if (in_t == T_I32) return pick_mode<J, int32_t, int32_t, false>(mode);
+    return nullptr;
+  }
+  if (acc_t == T_I64) {
+    if (in_t == T_I16) return pick_mode<J, int16_t, int64_t, false>(mode);
+    if (in_t == T_I32) return pick_mode<J, int32_t, int64_t, false>(mode);
+    if (in_t == T_I64) return pick_mode<J, int64_t, int64_t, false>(mode);
+  }
+  return nullptr;
+}
+
+GenKernel pick_generic(int J, int in_t, int acc_t, int mode, bool weight) {
+  switch (J) {
+    case 1: return pick_types<1>(in_t, acc_t, mode, weight);
+    case 2: return pick_types<2>(in_t, acc_t, mode, weight);
+    case 3: return pick_types<3>(in_t, acc_t, mode, weight);
+  }
+  return nullptr;
+}
+
+int type_size(int t) { return t == T_I16 ? 2 : (t == T_I32 ? 4 : 8); }
+
+struct PassPlan {
+  bool first6;
+  int J, r, in_t, acc_t, mode;
+  bool weight;
+  int64_t C;
+  size_t out_bytes;  // non-final passes only
+};
+
+// Build the pass schedule.  shots_bound: an upper bound on every basis' total
+// count (decides int32 vs int64 partial sums); weighted: FP64 path.
+std::vector<PassPlan> make_plan(int n, lre_count_kind kind, bool weighted, bool parity,
+                                int64_t shots_bound, bool aligned16) {
+  std::vector<PassPlan> plan;
+  int r = n, t = 0;
+  int64_t C = 1;
+  int in_t = (kind == LRE_COUNTS_I16) ? T_I16 : T_I32;
+  auto fits32 = [&](int tt) {
+    return shots_bound > 0 && (double)ipow(3, tt) * (double)shots_bound < 2147483647.0;
+  };
+  if (!weighted && n >= 6 && r > 6 && aligned16 && fits32(6)) {
+    PassPlan p{};
+    p.first6 = true;
+    p.J = 6;
+    p.r = r;
+    p.in_t = in_t;
+    p.acc_t = T_I32;
+    p.mode = M_STORE;
+    p.C = C;
+    p.out_bytes = (size_t)ipow(6, r - 6) * 4096 * 4;
+    plan.push_back(p);
+    r -= 6;
+    t += 6;
+    C *= 4096;
+    in_t = T_I32;
+  }
+  while (r > 0) {
+    const int jmax = weighted ? 2 : 3;
+    const int J = r < jmax ? r : jmax;
+    const bool last = (J == r);
+    t += J;
+    PassPlan p{};
+    p.first6 = false;
+    p.J = J;
+    p.r = r;
+    p.in_t = in_t;
+    p.weight = weighted && (in_t != T_F64);
+    p.acc_t = weighted ? T_F64 : (fits32(t) ? T_I32 : T_I64);
+    p.mode = last ? (parity ? M_PARITY : (weighted ? M_FINAL_W : M_FINAL_U)) : M_STORE;
+    p.C = C;
+    p.out_bytes = last ? 0 : (size_t)ipow(6, r - J) * (size_t)ipow(4, J) * C * type_size(p.acc_t);
+    plan.push_back(p);
+    in_t = p.acc_t;
+    r -= J;
+    C *= ipow(4, J);
+  }
+  return plan;
+}
+
+void plan_buffers(const std::vector<PassPlan> &plan, size_t &bufA, size_t &bufB) {
+  bufA = bufB = 0;
+  for (size_t k = 0; k < plan.size(); ++k) {
+    size_t &b = (k % 2 == 0) ? bufA : bufB;
+    if (plan[k].out_bytes > b) b = plan[k].out_bytes;
+  }
+}
+
+size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound) {
+  auto plan = make_plan(n, kind, weighted, false, shots_bound, true);
+  size_t a, b;
+  plan_buffers(plan, a, b);
+  size_t w = weighted ? round_up((size_t)ipow(3, n) * sizeof(double)) : 0;
+  return round_up(a) + round_up(b) + w;
+}
+
+__global__ void inv_shots_kernel(const int64_t *shots, double *w, int64_t B, int *status) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = shots[b];
+    if (s <= 0) latch(status, LRE_ERR_INVALID_ARG);
+    w[b] = s > 0 ? 1.0 / (double)s : 0.0;
+  }
+}
+
+lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
+  const bool weighted = a.shots != nullptr;
+  const bool parity = a.S != nullptr;
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(a.counts) & 15) == 0;
+  const int64_t bound = weighted ? 0 : a.shots_uniform;
+  auto plan = make_plan(a.n, a.kind, weighted, parity, bound, aligned16);
+  size_t bA, bB;
+  plan_buffers(plan, bA, bB);
+  char *p = static_cast<char *>(ws);
+  void *bufA = p;
+  void *bufB = p + round_up(bA);
+  double *wgt = reinterpret_cast<double *>(p + round_up(bA) + round_up(bB));
+  const size_t need = round_up(bA) + round_up(bB) + (weighted ? round_up((size_t)ipow(3, a.n) * 8) : 0);
+  if (need > ws_bytes) return LRE_ERR_OOM;
+  const int64_t B = ipow(3, a.n);
+  if (weighted) {
+    Launch L(ctx, "inv_shots", s);
+    inv_shots_kernel<<<256, 256, 0, s>>>(a.shots, wgt, B, ctx->d_status);
+  }
+  const void *in = a.counts;
+  for (size_t k = 0; k < plan.size(); ++k) {
+    const PassPlan &pp = plan[k];
+    void *out;
+    if (pp.mode == M_STORE)
+      out = (k % 2 == 0) ? bufA : bufB;
+    else
+      out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
+    if (pp.first6) {
+      const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
+      const size_t smem = 64 * P1_ZSTRIDE * sizeof(int32_t);
+      int grid = ctx->num_sms * 2;
+      if ((int64_t)grid > tiles) grid = (int)tiles;
+      Launch L(ctx, "fold_first6", s);
+      if (pp.in_t == T_I16) {
+        cudaFuncSetAttribute(fold_first6<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fold_first6<int16_t><<<grid, P1_THREADS, smem, s>>>(static_cast<const int16_t *>(in),
+                                                            static_cast<int32_t *>(out), pp.r, tiles);
+      } else {
+        cudaFuncSetAttribute(fold_first6<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fold_first6<int32_t><<<grid, P1_THREADS, smem, s>>>(static_cast<const int32_t *>(in),
+                                                            static_cast<int32_t *>(out), pp.r, tiles);
+      }
+    } else {
+      GenKernel kern = pick_generic(pp.J, pp.in_t, pp.acc_t, pp.mode, pp.weight);
+      if (!kern) return LRE_ERR_UNSUPPORTED;
+      GenParams gp;
+      gp.in = in;
+      gp.out = out;
+      gp.C = pp.C;
+      gp.n_oh = 1ll << (pp.r - pp.J);
+      gp.items = ipow(3, pp.r - pp.J) * gp.n_oh * pp.C;
+      gp.r = pp.r;
+      gp.n = a.n;
+      gp.wgt = wgt;
+      gp.shots = (double)a.shots_uniform;
+      gp.total = a.shots_uniform * B;
+      gp.status = ctx->d_status;
+      int64_t blocks = (gp.items + 255) / 256;
+      const int64_t cap = (int64_t)ctx->num_sms * 64;
+      if (blocks > cap) blocks = cap;
+      Launch L(ctx, pp.mode == M_STORE ? "fold_pass" : "fold_final", s);
+      kern<<<(unsigned)blocks, 256, 0, s>>>(gp);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fold pass launch");
+    in = out;
+  }
+  return LRE_OK;
+}
+
+}  // namespace lre

@@ -1,0 +1,92 @@
+// Internal declarations shared by the translation units of liblre.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lre.h"
+
+struct cusolverDnContext;
+struct cublasContext;
+
+struct lre_prof_entry {
+  const char *name;
+  cudaEvent_t start, stop;
+};
+
+struct lre_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t ws_limit = 0;        // 0 = unlimited
+  void *ws = nullptr;         // device workspace
+  size_t ws_bytes = 0;
+  int *d_status = nullptr;    // device-side latched error code (0 = none)
+  cusolverDnContext *solver = nullptr;
+  cublasContext *blas = nullptr;
+  std::string last_error;
+  bool prof = false;                      // record CUDA events around each launch
+  std::vector<lre_prof_entry> prof_pool;  // reused events
+  size_t prof_used = 0;
+  uint64_t launches = 0;                  // kernels of this library launched so far
+};
+
+namespace lre {
+
+// Status codes written by kernels into ctx->d_status (first writer wins).
+__device__ __forceinline__ void latch(int *status, int code) { atomicCAS(status, 0, code); }
+
+// Ensure ctx->ws holds at least `bytes` (respecting the cap).
+lre_status ensure_workspace(lre_ctx *ctx, size_t bytes);
+lre_status cuda_fail(lre_ctx *ctx, cudaError_t e, const char *where);
+
+// Brackets one launch (or one library call when own == false): counts our
+// own kernel launches and, when profiling is on, records a pair of events on
+// the launch stream.
+class Launch {
+ public:
+  Launch(lre_ctx *ctx, const char *name, cudaStream_t s, int own = 1);
+  ~Launch();
+
+ private:
+  lre_ctx *ctx_;
+  cudaStream_t s_;
+  long idx_ = -1;  // index into ctx->prof_pool (the pool may grow)
+};
+
+inline int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+// ---- step (i): counts -> S (int64) or theta (FP64) --------------------------
+struct FoldArgs {
+  const void *counts;
+  lre_count_kind kind;
+  int n;
+  const int64_t *shots;   // per-basis (device) or nullptr
+  int64_t shots_uniform;  // used when shots == nullptr
+  double *theta;          // final FP64 output (estimate mode) or nullptr
+  int64_t *S;             // final int64 output (parity-sum mode) or nullptr
+};
+size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound);
+lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s);
+
+// ---- step (ii): theta -> rho -------------------------------------------------
+size_t assemble_workspace_bytes(int n);
+lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
+                        cudaStream_t s);
+
+// ---- step (iii): rho -> physical rho ----------------------------------------
+lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,
+                       double *eig_mu, double *eig_rho, cudaStream_t s);
+
+// ---- ingest ------------------------------------------------------------------
+lre_status histogram_run(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,
+                         int64_t shots_per_basis, int n, void *counts, lre_count_kind kind,
+                         cudaStream_t s);
+
+}  // namespace lre

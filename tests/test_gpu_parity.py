@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (from the method's arithmetic):
+  * integer parity sums S and uniform-shot theta: bit-exact (theta is one
+    correctly rounded FP64 division of two exact integers on both sides);
+  * per-basis-shot theta: |dtheta| <= 1e-12 (FP64 sums in a different order);
+  * rho (complex64 output of an FP64 butterfly): relative Frobenius <= 1e-6;
+  * projection: relative Frobenius <= 1e-6 against the oracle's projection of
+    the same complex64 mu, spectra within 1e-9.
+"""
+import numpy as np
+import pytest
+
+from oracle import direct, project
+from synth import counts as sc
+from synth import states as st
+from tests.gpu_util import ctx_and_lre, need_gpu, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    lre, ctx = ctx_and_lre()
+    yield torch, lre, ctx
+    lre.lre_destroy(ctx)
+
+
+def _ginibre_counts(n, N, seed, dtype=np.int32):
+    rho = st.ginibre_state(n, 2, seed=seed)
+    thr = sc.cdf_thresholds(st.born_probabilities(st.pauli_expectations(rho), n))
+    return sc.sample_cdf(thr, N, seed=seed + 1, dtype=dtype)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("dtype", [np.int32, np.int16])
+def test_theta_bit_exact_and_rho(env, n, dtype):
+    torch, lre, ctx = env
+    N = 1000
+    counts = _ginibre_counts(n, N, seed=10 * n, dtype=dtype)
+    c = torch.from_numpy(counts).cuda()
+    theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+    rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda")
+    lre.lre_estimate(ctx, c, N, n, theta, rho)
+    lre.lre_sync(ctx)
+    t_ref = direct.estimate(counts, N, n)
+    np.testing.assert_array_equal(theta.cpu().numpy(), t_ref)
+    assert rel_fro(rho.cpu().numpy(), direct.mu(t_ref, n)) <= 1e-6
+
+
+@pytest.mark.parametrize("n,bound", [(3, 0), (6, 0), (7, 0), (7, 1000), (8, 1000)])
+def test_parity_sums_bit_exact(env, n, bound):
+    torch, lre, ctx = env
+    counts = _ginibre_counts(n, 1000, seed=77 + n)
+    S = torch.empty(4 ** n, dtype=torch.int64, device="cuda")
+    lre.lre_parity_sums(ctx, torch.from_numpy(counts).cuda(), n, S, row_total_bound=bound)
+    lre.lre_sync(ctx)
+    np.testing.assert_array_equal(S.cpu().numpy(), direct.parity_sums(counts, n)[0])
+
+
+@pytest.mark.parametrize("n", [2, 5, 7])
+def test_per_basis_shots(env, n):
+    torch, lre, ctx = env
+    rng = np.random.default_rng(n)
+    N = rng.integers(500, 10001, size=3 ** n)
+    probs = st.born_probabilities(st.pauli_expectations(st.ginibre_state(n, 3, seed=n)), n)
+    probs = np.clip(probs, 0, None)
+    probs /= probs.sum(axis=1, keepdims=True)
+    counts = np.stack([rng.multinomial(int(N[b]), probs[b]) for b in range(3 ** n)]).astype(np.int32)
+    theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+    lre.lre_estimate(ctx, torch.from_numpy(counts).cuda(), torch.from_numpy(N.astype(np.int64)).cuda(),
+                     n, theta)
+    lre.lre_sync(ctx)
+    np.testing.assert_allclose(theta.cpu().numpy(), direct.estimate(counts, N, n), atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_assemble_matches_direct_mu(env, n):
+    torch, lre, ctx = env
+    rng = np.random.default_rng(100 + n)
+    t = rng.uniform(-1, 1, 4 ** n)
+    t[0] = 1.0
+    rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda")
+    lre.lre_assemble(ctx, torch.from_numpy(t).cuda(), n, rho)
+    lre.lre_sync(ctx)
+    assert rel_fro(rho.cpu().numpy(), direct.mu(t, n)) <= 1e-6
+
+
+@pytest.mark.parametrize("n,N", [(1, 100), (2, 20), (3, 30), (5, 50), (7, 100)])
+def test_projection_matches_oracle(env, n, N):
+    torch, lre, ctx = env
+    counts = _ginibre_counts(n, N, seed=300 + n)
+    theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+    mu = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda")
+    lre.lre_estimate(ctx, torch.from_numpy(counts).cuda(), N, n, theta, mu)
+    out = torch.empty_like(mu)
+    em = torch.empty(2 ** n, dtype=torch.float64, device="cuda")
+    er = torch.empty(2 ** n, dtype=torch.float64, device="cuda")
+    lre.lre_project(ctx, mu, n, out, em, er)
+    lre.lre_sync(ctx)
+    mu_h = mu.cpu().numpy().astype(np.complex128)
+    ref, lam_mu, lam = project.smolin(mu_h)
+    assert rel_fro(out.cpu().numpy(), ref) <= 1e-6
+    np.testing.assert_allclose(em.cpu().numpy(), lam_mu, atol=1e-9)
+    np.testing.assert_allclose(er.cpu().numpy(), lam, atol=1e-9)
+    w = np.linalg.eigvalsh(out.cpu().numpy().astype(np.complex128))
+    assert w.min() > -1e-6 and abs(np.trace(out.cpu().numpy()) - 1) < 1e-5
+
+
+def test_projection_of_physical_state_is_identity(env):
+    torch, lre, ctx = env
+    n = 4
+    mu = torch.from_numpy(st.ginibre_state(n, 16, seed=5).astype(np.complex64)).cuda()
+    out = torch.empty_like(mu)
+    lre.lre_project(ctx, mu, n, out)
+    lre.lre_sync(ctx)
+    np.testing.assert_array_equal(out.cpu().numpy(), mu.cpu().numpy())
+
+
+def test_histogram_ingest(env):
+    torch, lre, ctx = env
+    n, B, S = 5, 243, 777
+    rng = np.random.default_rng(8)
+    rec = rng.integers(0, 2 ** n, size=(B, S)).astype(np.int16)
+    want = np.stack([np.bincount(r, minlength=2 ** n) for r in rec])
+    for dt in (torch.int32, torch.int16):
+        out = torch.empty((B, 2 ** n), dtype=dt, device="cuda")
+        lre.lre_histogram(ctx, torch.from_numpy(rec).cuda(), n, out)
+        lre.lre_sync(ctx)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_device_generators_match_cpu(env):
+    torch, lre, ctx = env
+    from synth import gen
+    n = 6
+    c = torch.empty((3 ** n, 2 ** n), dtype=torch.int16, device="cuda")
+    gen.gen_ghz(n, 0.05, 1000, 42, c)
+    np.testing.assert_array_equal(c.cpu().numpy(), sc.sample_ghz(n, 0.05, 1000, 42, dtype=np.int16))
+    bloch = st.haar_bloch_vectors(n, seed=3, shrink=0.95)
+    c32 = torch.empty((3 ** n, 2 ** n), dtype=torch.int32, device="cuda")
+    gen.gen_product(bloch, 500, 7, c32)
+    np.testing.assert_array_equal(c32.cpu().numpy(), sc.sample_product(bloch, 500, 7))
+    probs = st.born_probabilities(st.pauli_expectations(st.ginibre_state(4, 2, seed=1)), 4)
+    thr = sc.cdf_thresholds(probs)
+    c4 = torch.empty((81, 16), dtype=torch.int32, device="cuda")
+    gen.gen_cdf(torch.from_numpy(thr.view(np.int32)).cuda(), 4, 1000, 5, c4)
+    np.testing.assert_array_equal(c4.cpu().numpy(), sc.sample_cdf(thr, 1000, 5))
+
+
+def test_errors_and_latched_status(env):
+    torch, lre, ctx = env
+    n = 3
+    counts = torch.from_numpy(_ginibre_counts(n, 100, seed=1)).cuda()
+    theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+    with pytest.raises(lre.LreError) as e:
+        lre.lre_estimate(ctx, counts, 0, n, theta)
+    assert e.value.status == lre.LRE_ERR_INVALID_ARG
+    with pytest.raises(lre.LreError) as e:
+        lre.lre_estimate(ctx, counts, 100, 15, theta)
+    assert e.value.status == lre.LRE_ERR_UNSUPPORTED
+    lre.lre_estimate(ctx, counts, 101, n, theta)      # wrong shots: latched, not raised
+    with pytest.raises(lre.LreError) as e:
+        lre.lre_sync(ctx)
+    assert e.value.status == lre.LRE_ERR_SHOTS_MISMATCH
+    lre.lre_sync(ctx)                                # cleared
+    ctx2 = lre.lre_create(0)
+    try:
+        lre.lre_set_workspace_limit(ctx2, 1024)
+        big = torch.from_numpy(_ginibre_counts(8, 100, seed=2)).cuda()
+        th = torch.empty(4 ** 8, dtype=torch.float64, device="cuda")
+        with pytest.raises(lre.LreError) as e:
+            lre.lre_estimate(ctx2, big, 100, 8, th)
+        assert e.value.status == lre.LRE_ERR_OOM
+    finally:
+        lre.lre_destroy(ctx2)

@@ -280,3 +280,14 @@ def test_maximally_mixed_mse_law(n):
     assert abs(vals.mean() - want) < 4 * se, (vals.mean(), want, se)
     # a 1/(N 2^k) weight instead of 1/(N 3^k) would be far outside
     assert abs(vals.mean() - want) < 0.1 * want
+
+
+def test_entry_spot_values_match_full_direct_sum():
+    n = 5
+    rng = np.random.default_rng(12)
+    c = rng.multinomial(1000, np.ones(32) / 32, size=243).astype(np.int16)
+    S, _ = direct.parity_sums(c, n)
+    idx = rng.integers(0, 4 ** n, 64)
+    np.testing.assert_array_equal(direct.parity_sum_entries(n, idx, lambda b: c[b]), S[idx])
+    assert direct.compatible_bases(0, 1) == [0, 1, 2]
+    assert direct.compatible_bases(4 * 3 + 0, 2) == [6, 7, 8]   # Z(x)I: a_1 = Z
