@@ -193,7 +193,6 @@ def spot_check(torch, wl, theta, rho, n_entries=96, n_rho=32):
         dig = rng.integers(1, 4, size=n)
         dig[rng.choice(n, size=k, replace=False)] = 0
         idx.append(int(sum(int(dig[q]) << (2 * (n - 1 - q)) for q in range(n))))
-    idx[0] = 0
     want = direct.estimate_entries(n, idx, lambda b: cpu_rows(wl, b), wl["shots"])
     got = theta[torch.tensor(idx, device=theta.device)].cpu().numpy()
     ok_theta = bool(np.array_equal(got, want))
