@@ -207,6 +207,50 @@ def spot_check(torch, wl, theta, rho, n_entries=96, n_rho=32):
             "rho_entries": n_rho, "rho_max_rel_err": err}
 
 
+def run_e2e(args, wl, lre, torch, device, theta_dev):
+    """Same metric through lre_estimate_host: every step copies the step's
+    input from pinned host memory and reads theta and rho back."""
+    n, N = wl["n"], wl["shots"]
+    B, d = 3 ** n, 2 ** n
+    if wl["state"] == "ghz":
+        from synth import gen
+        rec = torch.empty((B, N), dtype=torch.int16, device=device)
+        gen.gen_ghz_records(n, wl["p"], wl["seed"], rec)
+        host_in = torch.empty((B, N), dtype=torch.int16, pin_memory=True)
+        host_in.copy_(rec)
+        del rec
+        kind, what = lre.LRE_HOST_RECORDS_U16, "uint16 shot records"
+    else:
+        c = make_counts(torch, wl, device)
+        host_in = torch.empty(c.shape, dtype=c.dtype, pin_memory=True)
+        host_in.copy_(c)
+        del c
+        kind = lre.LRE_HOST_COUNTS_I16 if wl["kind"] == "i16" else lre.LRE_HOST_COUNTS_I32
+        what = f"{wl['kind']} dense counts"
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    theta_h = torch.empty(4 ** n, dtype=torch.float64, pin_memory=True)
+    rho_h = torch.empty((d, d), dtype=torch.complex64, pin_memory=True)
+    ctx = lre.lre_create(device.index)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        lre.lre_estimate_host(ctx, host_in, kind, N, n, theta_h, rho_h, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lre.lre_estimate_host(ctx, host_in, kind, N, n, theta_h, rho_h, stream=stream)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    same = bool(torch.equal(theta_h, theta_dev.cpu())) if theta_dev is not None else None
+    lre.lre_destroy(ctx)
+    return {"value": round(B / dt, 1), "unit": "Pauli bases/s", "seconds_per_step": round(dt, 4),
+            "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+            "d2h_bytes_per_step": theta_h.numel() * 8 + rho_h.numel() * 8,
+            "input": f"pinned host {what}; lre_estimate_host (chunked H2D on a copy stream, "
+                     f"device ingest, fold, assembly, D2H theta+rho)",
+            "theta_equals_device_path": same}
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -282,6 +326,15 @@ def run_ours(args, wl):
     step_alg = B * (2 ** n) * count_bytes + 8 * 4 ** n * 2 + 8 * 4 ** n
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in per.items()}
     check = spot_check(torch, wl, theta, rho) if args.check and rank == 0 else None
+    lre.lre_destroy(ctx)
+    ctx = None
+    e2e = None
+    if not args.no_e2e:
+        theta_keep = theta
+        del counts, rho
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        e2e = run_e2e(args, wl, lre, torch, device, theta_keep)
 
     out = None
     if rank == 0:
@@ -302,13 +355,14 @@ def run_ours(args, wl):
                        "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+            "e2e": None,
             "kernels": kernels,
             "step_alg_bytes": step_alg,
             "step_alg_gbs": round(step_alg / (ms / 1e3) / 1e9, 1),
         }
         if check:
             out["parity"] = check
-    lre.lre_destroy(ctx)
+        out["e2e"] = e2e
     return out
 
 
@@ -345,6 +399,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     args = ap.parse_args()

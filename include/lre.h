@@ -63,6 +63,12 @@ typedef enum {
   LRE_COUNTS_I16 = 1  /* int16 counts (each count <= 32767)                   */
 } lre_count_kind;
 
+typedef enum {
+  LRE_HOST_COUNTS_I32 = 0,  /* host int32 counts [3^n][2^n]                        */
+  LRE_HOST_COUNTS_I16 = 1,  /* host int16 counts [3^n][2^n]                        */
+  LRE_HOST_RECORDS_U16 = 2  /* host uint16 shot records [3^n][shots]: outcome index */
+} lre_host_kind;
+
 typedef struct {
   float re, im;
 } lre_c64;
@@ -136,6 +142,19 @@ lre_status lre_project(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
 lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,
                          int64_t shots_per_basis, int n, void *counts, lre_count_kind kind,
                          lre_stream stream);
+
+/* Steps (i)+(ii) end to end from HOST memory.  host_in: pinned host buffer
+ * of `host_kind` (dense counts, or shot records that the ingest kernel
+ * histograms on the device); shots_uniform: shots per basis (> 0);
+ * theta_host: host FP64 [4^n]; rho_host: host complex64 [2^n][2^n] or NULL.
+ * The input is copied in row chunks on a copy stream owned by the context,
+ * overlapped with the ingest; the device work runs on `stream`; the call
+ * returns when theta (and rho) are in host memory, with any latched kernel
+ * error.  Device memory used: the counts (3^n 2^n x 2 or 4 bytes), theta, rho
+ * and the fold workspace, all held in the context's workspace. */
+lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind host_kind,
+                             int64_t shots_uniform, int n, double *theta_host, lre_c64 *rho_host,
+                             lre_stream stream);
 
 /* Synchronise `stream` and return (and clear) the first error latched by a
  * kernel since the last lre_sync. */

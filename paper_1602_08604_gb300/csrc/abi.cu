@@ -161,6 +161,11 @@ void lre_destroy(lre_ctx *ctx) {
   if (ctx->blas) cublasDestroy(reinterpret_cast<cublasHandle_t>(ctx->blas));
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);
+    if (ctx->ev_free[k]) cudaEventDestroy(ctx->ev_free[k]);
+  }
   for (auto &e : ctx->prof_pool) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);
@@ -249,6 +254,21 @@ lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_base
   if ((st = set_device(ctx)) != LRE_OK) return st;
   return histogram_run(ctx, records, num_bases, shots_per_basis, n, counts, kind,
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind host_kind,
+                             int64_t shots_uniform, int n, double *theta_host, lre_c64 *rho_host,
+                             lre_stream stream) {
+  if (check_ctx(ctx) != LRE_OK || !host_in || !theta_host || shots_uniform <= 0)
+    return LRE_ERR_INVALID_ARG;
+  lre_status st = check_n(n);
+  if (st != LRE_OK) return st;
+  if (host_kind != LRE_HOST_COUNTS_I32 && host_kind != LRE_HOST_COUNTS_I16 &&
+      host_kind != LRE_HOST_RECORDS_U16)
+    return LRE_ERR_INVALID_ARG;
+  if ((st = set_device(ctx)) != LRE_OK) return st;
+  return estimate_host_run(ctx, host_in, host_kind, shots_uniform, n, theta_host, rho_host,
+                           reinterpret_cast<cudaStream_t>(stream));
 }
 
 lre_status lre_sync(lre_ctx *ctx, lre_stream stream) {

@@ -1,0 +1,98 @@
+// lre_estimate_host: steps (i)+(ii) end to end from host memory.
+//
+// The input (dense counts or per-basis shot records) is streamed to the
+// device in row chunks on a copy stream owned by the context, each chunk's
+// copy overlapping the ingest of the previous one (records are histogrammed
+// into device counts by the ingest kernel).  The device path then runs
+// exactly as lre_estimate, and theta / rho are copied back.  Host buffers
+// should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to run
+// asynchronously; pageable memory works but serialises.
+#include <cuda_runtime.h>
+
+#include "lre_internal.cuh"
+
+namespace lre {
+namespace {
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, int64_t shots,
+                             int n, double *theta_host, lre_c64 *rho_host, cudaStream_t s) {
+  const int64_t B = ipow(3, n);
+  const int64_t d = 1ll << n;
+  const bool records = host_kind == LRE_HOST_RECORDS_U16;
+  const lre_count_kind ck = records ? (shots <= 32767 ? LRE_COUNTS_I16 : LRE_COUNTS_I32)
+                                    : static_cast<lre_count_kind>(host_kind);
+  const size_t csz = (ck == LRE_COUNTS_I16) ? 2 : 4;
+  const size_t counts_bytes = (size_t)B * d * csz;
+  const size_t theta_bytes = (size_t)ipow(4, n) * sizeof(double);
+  const size_t rho_bytes = rho_host ? (size_t)d * d * sizeof(lre_c64) : 0;
+  // chunk: a whole number of rows, about 256 MB of host input
+  const size_t row_in = records ? (size_t)shots * sizeof(uint16_t) : (size_t)d * csz;
+  int64_t rows = (int64_t)((256ull << 20) / row_in);
+  if (rows < 1) rows = 1;
+  if (rows > B) rows = B;
+  const size_t chunk_in = (size_t)rows * row_in;
+  const size_t fold_ws = fold_workspace_bytes(n, ck, false, shots);
+  const size_t asm_ws = rho_host ? assemble_workspace_bytes(n) : 0;
+  const size_t dev_ws = up256(fold_ws > asm_ws ? fold_ws : asm_ws);
+  const size_t need = dev_ws + up256(counts_bytes) + up256(theta_bytes) + up256(rho_bytes) +
+                      (records ? 2 * up256(chunk_in) : 0);
+  lre_status st = ensure_workspace(ctx, need);
+  if (st != LRE_OK) return st;
+  char *p = static_cast<char *>(ctx->ws);
+  void *ws = p;
+  char *counts = p + dev_ws;
+  double *theta = reinterpret_cast<double *>(counts + up256(counts_bytes));
+  lre_c64 *rho = reinterpret_cast<lre_c64 *>(reinterpret_cast<char *>(theta) + up256(theta_bytes));
+  char *stage[2] = {reinterpret_cast<char *>(rho) + up256(rho_bytes), nullptr};
+  stage[1] = stage[0] + up256(chunk_in);
+
+  cudaError_t e = cudaSuccess;
+  if (!ctx->copy_stream) {
+    e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&ctx->ev_copied[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_free[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+  }
+  cudaStream_t cs = ctx->copy_stream;
+  // the copy stream must not run ahead of work the caller queued on s
+  e = cudaEventRecord(ctx->ev_free[0], s);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_free[1], s);
+  const char *src = static_cast<const char *>(host_in);
+  for (int64_t r0 = 0, k = 0; r0 < B && e == cudaSuccess; r0 += rows, ++k) {
+    const int64_t nr = (r0 + rows <= B) ? rows : (B - r0);
+    const int slot = (int)(k & 1);
+    char *dst = records ? stage[slot] : counts + (size_t)r0 * d * csz;
+    e = cudaStreamWaitEvent(cs, ctx->ev_free[slot], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, src + (size_t)r0 * row_in, (size_t)nr * row_in, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied[slot], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_copied[slot], 0);
+    if (e == cudaSuccess && records) {
+      st = histogram_run(ctx, reinterpret_cast<const uint16_t *>(dst), nr, shots, n,
+                         counts + (size_t)r0 * d * csz, ck, s);
+      if (st != LRE_OK) return st;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_free[slot], s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host input streaming");
+  FoldArgs fa{counts, ck, n, nullptr, shots, theta, nullptr};
+  if ((st = fold_run(ctx, fa, ws, dev_ws, s)) != LRE_OK) return st;
+  if (rho_host && (st = assemble_run(ctx, theta, n, rho, ws, s)) != LRE_OK) return st;
+  e = cudaMemcpyAsync(theta_host, theta, theta_bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && rho_host) e = cudaMemcpyAsync(rho_host, rho, rho_bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host outputs");
+  int code = 0;
+  e = cudaMemcpy(&code, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && code != 0) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status");
+  return static_cast<lre_status>(code);
+}
+
+}  // namespace lre

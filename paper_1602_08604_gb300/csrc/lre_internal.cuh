@@ -31,6 +31,9 @@ struct lre_ctx {
   std::vector<lre_prof_entry> prof_pool;  // reused events
   size_t prof_used = 0;
   uint64_t launches = 0;                  // kernels of this library launched so far
+  cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
 };
 
 namespace lre {
@@ -83,6 +86,10 @@ lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
 // ---- step (iii): rho -> physical rho ----------------------------------------
 lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,
                        double *eig_mu, double *eig_rho, cudaStream_t s);
+
+// ---- end to end from host memory ---------------------------------------------
+lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, int64_t shots,
+                             int n, double *theta_host, lre_c64 *rho_host, cudaStream_t s);
 
 // ---- ingest ------------------------------------------------------------------
 lre_status histogram_run(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,

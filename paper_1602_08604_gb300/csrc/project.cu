@@ -113,6 +113,7 @@ __global__ void emit_kernel(const double2 *C, float2 *out, int64_t d) {
       const double2 w = lo[i][tx];
       v = make_double2(w.x, -w.y);
     }
+    if (r == c) v.y = 0.0;  // a Hermitian matrix has a real diagonal
     out[r * d + c] = make_float2((float)v.x, (float)v.y);
   }
 }
@@ -127,6 +128,7 @@ __global__ void emit_small(const double2 *C, float2 *out, int64_t d) {
       const double2 w = C[r + c * d];
       v = make_double2(w.x, -w.y);
     }
+    if (r == c) v.y = 0.0;
     out[e] = make_float2((float)v.x, (float)v.y);
   }
 }

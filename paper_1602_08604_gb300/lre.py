@@ -23,6 +23,10 @@ LRE_ERR_EIG_FAILED = 7
 LRE_COUNTS_I32 = 0
 LRE_COUNTS_I16 = 1
 
+LRE_HOST_COUNTS_I32 = 0
+LRE_HOST_COUNTS_I16 = 1
+LRE_HOST_RECORDS_U16 = 2
+
 # (name, restype, argtypes) for every symbol declared in include/lre.h
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -38,6 +42,7 @@ SIGNATURES = [
     ("lre_assemble", _i, [_p, _p, _i, _p, _p]),
     ("lre_project", _i, [_p, _p, _i, _p, _p, _p, _p]),
     ("lre_histogram", _i, [_p, _p, _i64, _i64, _i, _p, _i, _p]),
+    ("lre_estimate_host", _i, [_p, _p, _i, _i64, _i, _p, _p, _p]),
     ("lre_sync", _i, [_p, _p]),
     ("lre_status_string", ctypes.c_char_p, [_i]),
     ("lre_last_error", ctypes.c_char_p, [_p]),
@@ -155,6 +160,12 @@ def lre_histogram(ctx, records, n, counts, stream=None):
     B, S = records.shape
     _check(load().lre_histogram(ctx, _ptr(records), int(B), int(S), int(n), _ptr(counts),
                                 _kind(counts), _stream(stream)), ctx)
+
+
+def lre_estimate_host(ctx, host_in, host_kind, shots, n, theta_host, rho_host=None, stream=None):
+    """host_in / theta_host / rho_host: pinned CPU tensors (data pointers only)."""
+    _check(load().lre_estimate_host(ctx, _ptr(host_in), int(host_kind), int(shots), int(n),
+                                    _ptr(theta_host), _ptr(rho_host), _stream(stream)), ctx)
 
 
 def lre_sync(ctx, stream=None):

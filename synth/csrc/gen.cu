@@ -95,6 +95,36 @@ __global__ void gen_ghz_kernel(int n, uint32_t noise_thr, int64_t b0, int64_t nb
   }
 }
 
+// Shot records of the same GHZ sampler: rec[j][s] = outcome of shot s of basis b0 + j.
+__global__ void gen_ghz_records_kernel(int n, uint32_t noise_thr, int64_t b0, int64_t nb, int64_t shots,
+                                       uint32_t k0, uint32_t k1, uint16_t *__restrict__ rec) {
+  const int d = 1 << n;
+  const int64_t total = nb * shots;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / shots, s = e - j * shots;
+    const int64_t b = b0 + j;
+    uint32_t zmask = 0;
+    int ny = 0;
+    int64_t x = b;
+    for (int q = 0; q < n; ++q) {
+      const int a = (int)(x % 3);
+      x /= 3;
+      if (a == 2) zmask |= 1u << q;
+      if (a == 1) ++ny;
+    }
+    const uint32_t par = (uint32_t)((ny >> 1) & 1);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)b, STREAM_GHZ, 0u), k0, k1);
+    const uint32_t u = w.y & (uint32_t)(d - 1);
+    uint32_t o;
+    if (w.x < noise_thr) o = u;
+    else if (zmask) o = (u & ~zmask) | ((w.z & 1u) ? zmask : 0u);
+    else if (ny & 1) o = u;
+    else o = ((uint32_t)(__popc(u) & 1) != par) ? (u ^ 1u) : u;
+    rec[e] = (uint16_t)o;
+  }
+}
+
 template <typename OutT>
 __global__ void gen_product_kernel(const uint32_t *__restrict__ thr, int n, int64_t b0, int64_t nb,
                                    int64_t shots, uint32_t k0, uint32_t k1, OutT *__restrict__ counts) {
@@ -188,6 +218,16 @@ int synth_gen_product(const uint32_t *thr, int n, int64_t b0, int64_t nb, int64_
     int smem = launch_cfg(gen_product_kernel<int32_t>, n, nb, grid);
     gen_product_kernel<int32_t><<<grid, 512, smem, s>>>(thr, n, b0, nb, shots, k0, k1, (int32_t *)counts);
   }
+  return (int)cudaGetLastError();
+}
+
+int synth_gen_ghz_records(int n, uint32_t noise_thr, int64_t b0, int64_t nb, int64_t shots,
+                          uint64_t seed, uint16_t *rec, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  gen_ghz_records_kernel<<<sms * 8, 256, 0, s>>>(n, noise_thr, b0, nb, shots, (uint32_t)seed,
+                                                (uint32_t)(seed >> 32), rec);
   return (int)cudaGetLastError();
 }
 

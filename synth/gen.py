@@ -38,7 +38,8 @@ def lib():
         L.synth_gen_cdf.argtypes = [p, i, i64, i64, i64, u64, p, i, p]
         L.synth_gen_ghz.argtypes = [i, u32, i64, i64, i64, u64, p, i, p]
         L.synth_gen_product.argtypes = [p, i, i64, i64, i64, u64, p, i, p]
-        for f in (L.synth_gen_cdf, L.synth_gen_ghz, L.synth_gen_product):
+        L.synth_gen_ghz_records.argtypes = [i, u32, i64, i64, i64, u64, p, p]
+        for f in (L.synth_gen_cdf, L.synth_gen_ghz, L.synth_gen_product, L.synth_gen_ghz_records):
             f.restype = i
         _lib = L
     return _lib
@@ -83,3 +84,12 @@ def gen_product(bloch, shots, seed, counts, b0=0):
     torch.cuda.current_stream().synchronize()
     if rc != 0:
         raise RuntimeError(f"synth_gen_product: cuda error {rc}")
+
+
+def gen_ghz_records(n, p_noise, seed, records, b0=0):
+    """records: uint16-valued device tensor [bases][shots] (int16 storage)."""
+    thr = int(prob_threshold(p_noise))
+    nb, shots = records.shape
+    rc = lib().synth_gen_ghz_records(n, thr, b0, nb, shots, _seed(seed), records.data_ptr(), _stream())
+    if rc != 0:
+        raise RuntimeError(f"synth_gen_ghz_records: cuda error {rc}")

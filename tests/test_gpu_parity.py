@@ -111,7 +111,10 @@ def test_projection_matches_oracle(env, n, N):
 def test_projection_of_physical_state_is_identity(env):
     torch, lre, ctx = env
     n = 4
-    mu = torch.from_numpy(st.ginibre_state(n, 16, seed=5).astype(np.complex64)).cuda()
+    m = st.ginibre_state(n, 16, seed=5).astype(np.complex64)
+    m = np.triu(m) + np.triu(m, 1).conj().T          # exactly Hermitian in complex64
+    m[np.diag_indices(2 ** n)] = m.diagonal().real
+    mu = torch.from_numpy(m).cuda()
     out = torch.empty_like(mu)
     lre.lre_project(ctx, mu, n, out)
     lre.lre_sync(ctx)
@@ -175,3 +178,32 @@ def test_errors_and_latched_status(env):
         assert e.value.status == lre.LRE_ERR_OOM
     finally:
         lre.lre_destroy(ctx2)
+
+
+@pytest.mark.parametrize("n,kind", [(6, "records"), (7, "i16"), (8, "i32"), (3, "records")])
+def test_estimate_host_matches_device_path(env, n, kind):
+    """End to end from pinned host memory (records histogrammed on device)
+    gives the same bits as the device path and the oracle."""
+    torch, lre, ctx = env
+    from synth import gen
+    N = 1000
+    if kind == "records":
+        rec_dev = torch.empty((3 ** n, N), dtype=torch.int16, device="cuda")
+        gen.gen_ghz_records(n, 0.05, 31, rec_dev)
+        rec = rec_dev.cpu().numpy().view(np.uint16)
+        np.testing.assert_array_equal(rec, sc.ghz_sample_outcomes(n, int(sc.prob_threshold(0.05)), N, 31,
+                                                                  np.arange(3 ** n)))
+        host_in = torch.from_numpy(rec.view(np.int16)).pin_memory()
+        counts = np.stack([np.bincount(r, minlength=2 ** n) for r in rec.astype(np.int64)]).astype(np.int32)
+        hk = lre.LRE_HOST_RECORDS_U16
+    else:
+        dt = np.int16 if kind == "i16" else np.int32
+        counts = _ginibre_counts(n, N, seed=n, dtype=dt)
+        host_in = torch.from_numpy(counts).pin_memory()
+        hk = lre.LRE_HOST_COUNTS_I16 if kind == "i16" else lre.LRE_HOST_COUNTS_I32
+    th = torch.empty(4 ** n, dtype=torch.float64).pin_memory()
+    rh = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64).pin_memory()
+    lre.lre_estimate_host(ctx, host_in, hk, N, n, th, rh)
+    t_ref = direct.estimate(counts, N, n)
+    np.testing.assert_array_equal(th.numpy(), t_ref)
+    assert rel_fro(rh.numpy(), direct.mu(t_ref, n)) <= 1e-6
