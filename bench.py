@@ -31,6 +31,9 @@ WORKLOADS = {
     "n12": dict(n=12, state="product", shrink=0.95, shots=4096, kind="i32", seed=12,
                 desc="n=12 product of Haar single-qubit states, 5% depolarising, 531441 bases x "
                      "4096 outcomes, 4096 shots/basis, int32 counts"),
+    "n12s": dict(n=12, state="ghz", p=0.05, shots=1000, kind="i16", seed=12,
+                 desc="n=12 GHZ+5% white noise, 531441 bases x 4096 outcomes, 1000 shots/basis, "
+                      "int16 counts (profiling-size case of the n=14 kernels)"),
     "n10": dict(n=10, state="ghz", p=0.10, shots=1000, kind="i32", seed=10,
                 desc="n=10 GHZ+10% white noise, 59049 bases x 1024 outcomes, 1000 shots/basis, int32"),
 }
@@ -168,6 +171,8 @@ def oracle_sample(wl, seconds_target=15.0, max_bases=None):
     diag = np.zeros(P, np.int64)
     probe = 16
     rows = cpu_rows(wl, np.arange(probe))
+    # first call builds the oracle's 2^n x 2^n nonzero matrix (kept for later calls)
+    direct.parity_sums(rows[:1], n, b0=0, b1=1, S=np.zeros(P, np.int64), diag=np.zeros(P, np.int64))
     t0 = time.perf_counter()
     direct.parity_sums(rows, n, b0=0, b1=probe, S=S, diag=diag)
     dt = time.perf_counter() - t0

@@ -216,11 +216,19 @@ lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, c
   if ((st = set_device(ctx)) != LRE_OK) return st;
   const size_t f = fold_workspace_bytes(n, kind, shots != nullptr, shots ? 0 : shots_uniform);
   const size_t a = rho ? assemble_workspace_bytes(n) : 0;
-  if ((st = ensure_workspace(ctx, f > a ? f : a)) != LRE_OK) return st;
+  const size_t shared = f > a ? f : a;
+  // uniform shots: rho is assembled from the exact integers T = S 3^(n-k)
+  const bool int_asm = rho && !shots;
+  const size_t tbytes = int_asm ? (((size_t)8 << (2 * n)) + 255) & ~(size_t)255 : 0;
+  if ((st = ensure_workspace(ctx, shared + tbytes)) != LRE_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int64_t *T = int_asm ? reinterpret_cast<int64_t *>(static_cast<char *>(ctx->ws) + shared) : nullptr;
   FoldArgs fa{counts, kind, n, shots, shots_uniform, theta, nullptr};
-  if ((st = fold_run(ctx, fa, ctx->ws, ctx->ws_bytes, s)) != LRE_OK) return st;
-  if (rho) st = assemble_run(ctx, theta, n, rho, ctx->ws, s);
+  fa.T = T;
+  if ((st = fold_run(ctx, fa, ctx->ws, shared, s)) != LRE_OK) return st;
+  if (rho)
+    st = int_asm ? assemble_int_run(ctx, T, n, shots_uniform, rho, ctx->ws, s)
+                 : assemble_run(ctx, theta, n, rho, ctx->ws, s);
   return st;
 }
 

@@ -3,15 +3,24 @@
 //
 // Per qubit the map from the Pauli letter coefficients (I, X, Y, Z) to the
 // 2x2 block entries (row bit r, column bit c) is
-//     (0,0) = (I + Z)/2   (0,1) = (X - iY)/2   (1,0) = (X + iY)/2   (1,1) = (I - Z)/2
-// so rho = M^{(x)n} t.  The paper instead sums, for each output element, the
-// 2^n strings sharing its nonzero pattern (Sec. IV, the 2^n x-mask groups);
-// the butterfly reaches the same sums in O(n 4^n).  Passes transform J <= 2
-// qubits each, lowest qubit first, in FP64; the last pass rounds once to
-// complex64 and writes rho row-major.
+//     (0,0) = I + Z   (0,1) = X - iY   (1,0) = X + iY   (1,1) = I - Z
+// (times 1/2), so rho = 2^-n M^{(x)n} t.  The paper instead sums, for each
+// output element, the 2^n strings sharing its nonzero pattern (Sec. IV, the
+// 2^n x-mask groups); the butterfly reaches the same sums in O(n 4^n).
 //
-// Layout after t qubits are done: [P_hi in 4^(n-t)][R_lo in 2^t][C_lo in 2^t]
-// (complex128), so the final layout (t = n) is rho[R][C].
+// Two number types run the same passes:
+//   * FP64 (lre_assemble on an arbitrary theta): FP64 butterflies with the
+//     1/2 per qubit, rounded once to complex64 at the end;
+//   * exact int64 (lre_estimate with uniform shots): the fold hands over
+//     T_i = S_i 3^(n-k_i) = t_i N 3^n, integers; the butterflies are exact
+//     integer adds and the last pass scales by 1/(2^n N 3^n) once.  GB300's
+//     FP64 rate is far below its integer rate, and this path is also exact
+//     until that single scaling.
+//
+// Layout after t qubits are done: [P_hi in 4^(n-t)][R_lo in 2^t][C_lo in 2^t],
+// so the final layout (t = n) is rho[R][C].  For n >= 10 the passes are
+// shared-memory tiled (6 qubits, then 4 at a time); smaller n and the
+// leftover qubits use register passes of 1-2 qubits.
 #include <cuda_runtime.h>
 
 #include "lre_internal.cuh"
@@ -19,25 +28,86 @@
 namespace lre {
 namespace {
 
+struct NumF64 {
+  using V = double2;
+  using In = double;
+};
+struct NumI64 {
+  using V = longlong2;
+  using In = long long;
+};
+
+struct LastScale {
+  float sh, sl;  // 1/(2^n N 3^n) = sh + sl (integer path only)
+};
+
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ longlong2 mk(long long a, long long b) { return make_longlong2(a, b); }
+
+// One qubit of the butterfly on (I, X, Y, Z) -> (00, 01, 10, 11).
+//   -i*Y = (Y.y, -Y.x);  +i*Y = (-Y.y, Y.x)
+__device__ __forceinline__ void m_qubit(double2 vI, double2 vX, double2 vY, double2 vZ, double2 &o00,
+                                        double2 &o01, double2 &o10, double2 &o11) {
+  o00 = mk(0.5 * (vI.x + vZ.x), 0.5 * (vI.y + vZ.y));
+  o11 = mk(0.5 * (vI.x - vZ.x), 0.5 * (vI.y - vZ.y));
+  o01 = mk(0.5 * (vX.x + vY.y), 0.5 * (vX.y - vY.x));
+  o10 = mk(0.5 * (vX.x - vY.y), 0.5 * (vX.y + vY.x));
+}
+__device__ __forceinline__ void m_qubit(longlong2 vI, longlong2 vX, longlong2 vY, longlong2 vZ,
+                                        longlong2 &o00, longlong2 &o01, longlong2 &o10, longlong2 &o11) {
+  o00 = mk(vI.x + vZ.x, vI.y + vZ.y);
+  o11 = mk(vI.x - vZ.x, vI.y - vZ.y);
+  o01 = mk(vX.x + vY.y, vX.y - vY.x);
+  o10 = mk(vX.x - vY.y, vX.y + vY.x);
+}
+
+__device__ __forceinline__ double2 load_first(const double *in, int64_t i) { return mk(__ldg(in + i), 0.0); }
+__device__ __forceinline__ longlong2 load_first(const long long *in, int64_t i) {
+  return mk(__ldg(in + i), 0ll);
+}
+
+// int64 -> float of v * (sh + sl), error about half an ulp of the float
+__device__ __forceinline__ float scaled(long long v, const LastScale &s) {
+  const float vh = (float)v;
+  const float vl = (float)(v - (long long)vh);
+  return __fmaf_rn(vh, s.sh, __fmaf_rn(vh, s.sl, vl * s.sh));
+}
+__device__ __forceinline__ float2 to_c64(double2 v, const LastScale &) {
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ float2 to_c64(longlong2 v, const LastScale &s) {
+  return make_float2(scaled(v.x, s), scaled(v.y, s));
+}
+
+template <typename V>
+__device__ __forceinline__ void m2(V (&v)[16]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    V a, b, c, d;
+    m_qubit(v[4 * h + 0], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3], a, b, c, d);
+    v[4 * h + 0] = a; v[4 * h + 1] = b; v[4 * h + 2] = c; v[4 * h + 3] = d;
+  }
+#pragma unroll
+  for (int u0 = 0; u0 < 4; ++u0) {
+    V a, b, c, d;
+    m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
+    v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
+  }
+}
+
 struct AsmParams {
   const void *in;
   void *out;
   int t;          // qubits already transformed
   int n;
   int64_t items;  // 4^(n-t-J) * 4^t
+  LastScale scale;
 };
 
-__device__ __forceinline__ void m_qubit(double2 vI, double2 vX, double2 vY, double2 vZ, double2 &o00,
-                                        double2 &o01, double2 &o10, double2 &o11) {
-  o00 = make_double2(0.5 * (vI.x + vZ.x), 0.5 * (vI.y + vZ.y));
-  o11 = make_double2(0.5 * (vI.x - vZ.x), 0.5 * (vI.y - vZ.y));
-  // -i*vY = (vY.y, -vY.x);  +i*vY = (-vY.y, vY.x)
-  o01 = make_double2(0.5 * (vX.x + vY.y), 0.5 * (vX.y - vY.x));
-  o10 = make_double2(0.5 * (vX.x - vY.y), 0.5 * (vX.y + vY.x));
-}
-
-template <int J, bool FIRST, bool LAST>
+// Register pass over J <= 2 qubits: one thread per (P', R_lo, C_lo).
+template <class Num, int J, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
+  using V = typename Num::V;
   constexpr int NP = 1 << (2 * J);
   const int t = P.t;
   const int tp = t + J;
@@ -47,27 +117,26 @@ __global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
     const int64_t L = item & (L4 - 1);
     const int64_t Pp = item >> (2 * t);
     const int64_t R_lo = L >> t, C_lo = L & ((1ll << t) - 1);
-    double2 v[NP];
+    V v[NP];
     const int64_t ibase = Pp * NP * L4 + L;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      if constexpr (FIRST) {
-        v[p] = make_double2(__ldg(static_cast<const double *>(P.in) + ibase + p * L4), 0.0);
-      } else {
-        v[p] = __ldg(static_cast<const double2 *>(P.in) + ibase + p * L4);
-      }
+      if constexpr (FIRST)
+        v[p] = load_first(static_cast<const typename Num::In *>(P.in), ibase + p * L4);
+      else
+        v[p] = static_cast<const V *>(P.in)[ibase + p * L4];
     }
     // digit 0 (qubit t): index p = p1*4 + p0 -> u0 = 2 r0 + c0
 #pragma unroll
     for (int h = 0; h < NP / 4; ++h) {
-      double2 a, b, c, d;
+      V a, b, c, d;
       m_qubit(v[4 * h + 0], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3], a, b, c, d);
       v[4 * h + 0] = a; v[4 * h + 1] = b; v[4 * h + 2] = c; v[4 * h + 3] = d;
     }
     if constexpr (J == 2) {
 #pragma unroll
       for (int u0 = 0; u0 < 4; ++u0) {
-        double2 a, b, c, d;
+        V a, b, c, d;
         m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
         v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
       }
@@ -89,36 +158,176 @@ __global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
       const int64_t R = ((int64_t)rj << t) | R_lo;
       const int64_t Cc = ((int64_t)cj << t) | C_lo;
       const int64_t o = obase + R * W + Cc;
-      if constexpr (LAST) {
-        static_cast<float2 *>(P.out)[o] = make_float2((float)v[u].x, (float)v[u].y);
-      } else {
-        static_cast<double2 *>(P.out)[o] = v[u];
-      }
+      if constexpr (LAST)
+        static_cast<float2 *>(P.out)[o] = to_c64(v[u], P.scale);
+      else
+        static_cast<V *>(P.out)[o] = v[u];
     }
   }
 }
 
-template <int J>
-void launch(bool first, bool last, const AsmParams &p, int grid, cudaStream_t s) {
-  if (first && last) assemble_pass<J, true, true><<<grid, 256, 0, s>>>(p);
-  else if (first) assemble_pass<J, true, false><<<grid, 256, 0, s>>>(p);
-  else if (last) assemble_pass<J, false, true><<<grid, 256, 0, s>>>(p);
-  else assemble_pass<J, false, false><<<grid, 256, 0, s>>>(p);
+// ---------------------------------------------------------------------------
+// Shared-memory tiled passes (n >= 10): a 6-qubit first pass over contiguous
+// blocks of 4096 coefficients, then 4-qubit passes over 16-column strips.
+// Each thread holds 16 complex values (two qubits) per round; rounds
+// exchange through shared memory (one padding element per 16: at most 4
+// wavefronts per 16-byte warp access).
+// ---------------------------------------------------------------------------
+constexpr int TILE_SMEM = (4096 + 256) * 16;
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// First pass: qubits 0..5 of each block of 4096 coefficients ->
+// [R_lo 64][C_lo 64] per block.
+template <class Num>
+__global__ void __launch_bounds__(256) assemble_low6(const typename Num::In *__restrict__ in,
+                                                    typename Num::V *__restrict__ out, int64_t blocks) {
+  using V = typename Num::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *S = reinterpret_cast<V *>(smem_raw);  // 4096 + 256 padded entries
+  const int tid = threadIdx.x;
+  for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int i = tid + 256 * k;
+      S[pad16(i)] = load_first(in, blk * 4096 + i);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int sh = 4 * r;
+      const int lo = tid & ((1 << sh) - 1), hi = tid >> sh;
+      V v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = S[pad16(lo | (u << sh) | (hi << (sh + 4)))];
+      m2(v);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) S[pad16(lo | (u << sh) | (hi << (sh + 4)))] = v[u];
+      __syncthreads();
+    }
+    // S[pos], pos digit q = 2 r_q + c_q  ->  out[R_lo * 64 + C_lo]
+    V *dst = out + blk * 4096;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int o = tid + 256 * k;
+      const int R = o >> 6, C = o & 63;
+      int pos = 0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) pos |= ((((R >> q) & 1) << 1) | ((C >> q) & 1)) << (2 * q);
+      dst[o] = S[pad16(pos)];
+    }
+    __syncthreads();
+  }
 }
 
-}  // namespace
-
-size_t assemble_workspace_bytes(int n) {
-  const size_t one = ((size_t)1 << (2 * n)) * sizeof(double2);
-  return 2 * ((one + 255) & ~(size_t)255);
+// 4-qubit pass over qubits t..t+3 (t >= 6): unit = (P', R_lo, 16 consecutive
+// C_lo).  Input [P'][p 256][R_lo][C_lo]; output [P'][R'][C'] with
+// R' = (rJ << t) | R_lo, C' = (cJ << t) | C_lo.
+template <class Num, bool LAST>
+__global__ void __launch_bounds__(256) assemble_high4(const typename Num::V *__restrict__ in,
+                                                     void *__restrict__ out, int t, int64_t units,
+                                                     LastScale scale) {
+  using V = typename Num::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *S = reinterpret_cast<V *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int64_t side = 1ll << t;        // 2^t
+  const int64_t L4 = side * side;       // 4^t
+  const int64_t per_p = L4 / 16;        // units per P'
+  const int64_t W = side << 4;          // 2^(t+4)
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t Pp = u / per_p;
+    const int64_t L0 = (u - Pp * per_p) * 16;  // first L of the strip
+    const int64_t R_lo = L0 >> t, C0 = L0 & (side - 1);
+    const V *src = in + Pp * 256 * L4 + L0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int e = tid + 256 * k;  // e = p * 16 + l
+      S[pad16(e)] = src[(int64_t)(e >> 4) * L4 + (e & 15)];
+    }
+    __syncthreads();
+    const int l = tid & 15, h = tid >> 4;
+    V v[16];
+    // round 1: digits 0,1 of p (p = d0 + 4 d1 + 16 (d2 + 4 d3))
+#pragma unroll
+    for (int w = 0; w < 16; ++w) v[w] = S[pad16(((w | (h << 4)) << 4) | l)];
+    m2(v);
+#pragma unroll
+    for (int w = 0; w < 16; ++w) S[pad16(((w | (h << 4)) << 4) | l)] = v[w];
+    __syncthreads();
+    // round 2: digits 2,3 for fixed (u0,u1) = h
+#pragma unroll
+    for (int w = 0; w < 16; ++w) v[w] = S[pad16(((h | (w << 4)) << 4) | l)];
+    m2(v);
+    const int r0 = (h >> 1) & 1, c0 = h & 1, r1 = (h >> 3) & 1, c1 = (h >> 2) & 1;
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+      const int r2 = (w >> 1) & 1, c2 = w & 1, r3 = (w >> 3) & 1, c3 = (w >> 2) & 1;
+      const int64_t rJ = r0 | (r1 << 1) | (r2 << 2) | (r3 << 3);
+      const int64_t cJ = c0 | (c1 << 1) | (c2 << 2) | (c3 << 3);
+      const int64_t o = Pp * W * W + ((rJ << t) | R_lo) * W + ((cJ << t) | (C0 + l));
+      if constexpr (LAST)
+        static_cast<float2 *>(out)[o] = to_c64(v[w], scale);
+      else
+        static_cast<V *>(out)[o] = v[w];
+    }
+    __syncthreads();
+  }
 }
 
-lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
-                        cudaStream_t s) {
-  const size_t one = (((size_t)1 << (2 * n)) * sizeof(double2) + 255) & ~(size_t)255;
+template <class Num, int J>
+void launch_reg(bool first, bool last, const AsmParams &p, int grid, cudaStream_t s) {
+  if (first && last) assemble_pass<Num, J, true, true><<<grid, 256, 0, s>>>(p);
+  else if (first) assemble_pass<Num, J, true, false><<<grid, 256, 0, s>>>(p);
+  else if (last) assemble_pass<Num, J, false, true><<<grid, 256, 0, s>>>(p);
+  else assemble_pass<Num, J, false, false><<<grid, 256, 0, s>>>(p);
+}
+
+template <class Num>
+lre_status run_passes(lre_ctx *ctx, const typename Num::In *in0, int n, lre_c64 *rho, void *ws,
+                      LastScale scale, cudaStream_t s) {
+  using V = typename Num::V;
+  const size_t one = (((size_t)1 << (2 * n)) * sizeof(V) + 255) & ~(size_t)255;
   char *bufs[2] = {static_cast<char *>(ws), static_cast<char *>(ws) + one};
-  const void *in = theta;
+  const void *in = in0;
   int t = 0, k = 0;
+  if (n >= 10) {
+    const int64_t blocks = 1ll << (2 * (n - 6));
+    int grid = ctx->num_sms * 4;
+    if (grid > blocks) grid = (int)blocks;
+    {
+      Launch L(ctx, "assemble_low6", s);
+      cudaFuncSetAttribute(assemble_low6<Num>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+      assemble_low6<Num><<<grid, 256, TILE_SMEM, s>>>(in0, reinterpret_cast<V *>(bufs[0]), blocks);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble_low6 launch");
+    in = bufs[0];
+    t = 6;
+    k = 1;
+    while (n - t >= 4) {
+      const bool last = (t + 4 == n);
+      const int64_t units = (1ll << (2 * (n - t - 4))) * ((1ll << (2 * t)) / 16);
+      int g = ctx->num_sms * 4;
+      if (g > units) g = (int)units;
+      void *out = last ? static_cast<void *>(rho) : static_cast<void *>(bufs[k & 1]);
+      {
+        Launch L(ctx, last ? "assemble_high4_last" : "assemble_high4", s);
+        if (last) {
+          cudaFuncSetAttribute(assemble_high4<Num, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+          assemble_high4<Num, true><<<g, 256, TILE_SMEM, s>>>(static_cast<const V *>(in), out, t, units, scale);
+        } else {
+          cudaFuncSetAttribute(assemble_high4<Num, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+          assemble_high4<Num, false><<<g, 256, TILE_SMEM, s>>>(static_cast<const V *>(in), out, t, units, scale);
+        }
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble_high4 launch");
+      in = out;
+      t += 4;
+      ++k;
+    }
+  }
   while (t < n) {
     const int J = (n - t) >= 2 ? 2 : 1;
     const bool first = (t == 0), last = (t + J == n);
@@ -128,13 +337,14 @@ lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
     p.t = t;
     p.n = n;
     p.items = (1ll << (2 * (n - t - J))) << (2 * t);
+    p.scale = scale;
     int64_t blocks = (p.items + 255) / 256;
     const int64_t cap = (int64_t)ctx->num_sms * 32;
     if (blocks > cap) blocks = cap;
     {
       Launch L(ctx, last ? "assemble_last" : "assemble_pass", s);
-      if (J == 2) launch<2>(first, last, p, (int)blocks, s);
-      else launch<1>(first, last, p, (int)blocks, s);
+      if (J == 2) launch_reg<Num, 2>(first, last, p, (int)blocks, s);
+      else launch_reg<Num, 1>(first, last, p, (int)blocks, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble pass launch");
@@ -143,6 +353,28 @@ lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
     ++k;
   }
   return LRE_OK;
+}
+
+}  // namespace
+
+size_t assemble_workspace_bytes(int n) {
+  const size_t one = ((size_t)1 << (2 * n)) * 16;  // complex128 or int64 pair
+  return 2 * ((one + 255) & ~(size_t)255);
+}
+
+lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
+                        cudaStream_t s) {
+  return run_passes<NumF64>(ctx, theta, n, rho, ws, LastScale{0.f, 0.f}, s);
+}
+
+lre_status assemble_int_run(lre_ctx *ctx, const int64_t *T, int n, int64_t shots, lre_c64 *rho,
+                            void *ws, cudaStream_t s) {
+  // 1 / (2^n N 3^n) split into two floats
+  const double scale = 1.0 / ((double)(1ll << n) * (double)shots * (double)ipow(3, n));
+  LastScale ls;
+  ls.sh = (float)scale;
+  ls.sl = (float)(scale - (double)ls.sh);
+  return run_passes<NumI64>(ctx, reinterpret_cast<const long long *>(T), n, rho, ws, ls, s);
 }
 
 }  // namespace lre

@@ -22,9 +22,12 @@
 // so the last pass leaves theta in the canonical order of Eq. (5).
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
 #include <vector>
 
 #include "lre_internal.cuh"
+#include "sm103.cuh"
 
 namespace lre {
 namespace {
@@ -157,6 +160,231 @@ __global__ void __launch_bounds__(P1_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
+// The same first pass as a warp-specialised TMA pipeline (the default).
+//   warp 0      producer: one 2D TMA load per sub-tile (81 rows x 64
+//               outcomes = the two top ternary digits of the tile fixed) into
+//               a ring of R shared-memory slots, completion on mbarriers.
+//   warps 1..6  level A: one sub-tile per warp, lane = (a3, olB) for 24
+//               lanes, 27 rows x 8 outcomes from shared memory -> 64 partial
+//               sums -> exchange buffer Z[tile parity].
+//   warps 7..8  level B: one thread per level-A Pauli triple, 27 x 8
+//               partials -> 64 outputs -> HBM.
+// Loads never sit in registers, so up to R sub-tiles (R x 10.4 KB for int16)
+// are in flight per SM while the ALU warps work.  Every wait is bounded; a
+// timed-out wait latches LRE_ERR_TIMEOUT and the CTA drains and exits.
+// ---------------------------------------------------------------------------
+constexpr int PIPE_A_WARPS = 5;
+constexpr int PIPE_THREADS = 32 * (1 + PIPE_A_WARPS + 2);
+constexpr int SUB_ROWS = 81;
+constexpr int Z_WORDS = 64 * P1_ZSTRIDE;
+
+// Ring slots are owned by level-A warps (RW per warp): every wait is then at
+// most one barrier phase ahead of the last completed one, which is what the
+// parity test of mbarrier.try_wait.parity can tell apart.
+template <typename InT>
+struct PipeCfg {
+  static constexpr int RW = sizeof(InT) == 2 ? 2 : 1;  // slots per level-A warp
+  static constexpr int R = PIPE_A_WARPS * RW;           // ring slots
+  static constexpr int SUB_BYTES = SUB_ROWS * 64 * (int)sizeof(InT);
+  static constexpr int RING_BYTES = R * SUB_BYTES;
+  static constexpr int Z_OFF = RING_BYTES;
+  static constexpr int BAR_OFF = Z_OFF + 2 * Z_WORDS * 4;
+  static constexpr int SMEM = BAR_OFF + (2 * R + 4) * 8 + 16 + 1024;  // + alignment slack
+};
+
+template <typename InT>
+__device__ __forceinline__ void lds_row8(const InT *p, int32_t (&v)[8]);
+
+template <>
+__device__ __forceinline__ void lds_row8<int16_t>(const int16_t *p, int32_t (&v)[8]) {
+  const uint4 u = *reinterpret_cast<const uint4 *>(p);
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
+    v[2 * k + 1] = ((int32_t)w[k]) >> 16;
+  }
+}
+
+template <>
+__device__ __forceinline__ void lds_row8<int32_t>(const int32_t *p, int32_t (&v)[8]) {
+  const int4 a = reinterpret_cast<const int4 *>(p)[0];
+  const int4 b = reinterpret_cast<const int4 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(PIPE_THREADS, 1)
+    fold_first6_pipe(const __grid_constant__ CUtensorMap tmap, int32_t *__restrict__ out, int n,
+                     int64_t tile_begin, int64_t tile_end, int64_t row_base, int *status) {
+  using Cfg = PipeCfg<InT>;
+  constexpr int R = Cfg::R;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // TMA destinations must be 128-byte aligned: align the base explicitly
+  uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
+  InT *ring = reinterpret_cast<InT *>(smem);
+  int32_t *Z = reinterpret_cast<int32_t *>(smem + Cfg::Z_OFF);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + Cfg::BAR_OFF);
+  uint64_t *empty = full + R;
+  uint64_t *zfull = empty + R;
+  uint64_t *zempty = zfull + 2;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(zempty + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_oh = (1ll << n) >> 6;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < R; ++i) {
+      sm103::mbar_init(&full[i], 1);
+      sm103::mbar_init(&empty[i], 32);
+    }
+    for (int b = 0; b < 2; ++b) {
+      sm103::mbar_init(&zfull[b], 9 * 32);
+      sm103::mbar_init(&zempty[b], 64);
+    }
+    *abort_flag = 0;
+    sm103::fence_barrier_init();
+  }
+  __syncthreads();
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    latch(status, LRE_ERR_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // sub-tile g goes to warp g % NA, its j-th item (j = g / NA), slot
+      // w*RW + j % RW, fill f = j / RW of that slot
+      int64_t g = 0;
+      for (int64_t tile = tile_begin + blockIdx.x; tile < tile_end && !*abort_flag; tile += gridDim.x) {
+        const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
+        for (int s = 0; s < 9; ++s, ++g) {
+          const int w = (int)(g % PIPE_A_WARPS);
+          const int64_t j = g / PIPE_A_WARPS;
+          const int slot = w * Cfg::RW + (int)(j % Cfg::RW);
+          const int64_t f = j / Cfg::RW;
+          if (f > 0 && !sm103::mbar_wait(&empty[slot], (uint32_t)((f - 1) & 1), abort_flag)) {
+            give_up();
+            break;
+          }
+          sm103::mbar_arrive_expect_tx(&full[slot], Cfg::SUB_BYTES);
+          sm103::tma_load_2d(ring + (size_t)slot * (Cfg::SUB_BYTES / sizeof(InT)), &tmap, (int)(oh * 64),
+                             (int)(ah * 729 + s * SUB_ROWS - row_base), &full[slot]);
+        }
+      }
+      // drain: every issued load must land before the CTA may exit; only the
+      // last fill of each slot can still be in flight
+      for (int slot = 0; slot < R; ++slot) {
+        const int w = slot / Cfg::RW, r = slot % Cfg::RW;
+        // number of items of warp w issued: ceil((g - w) / NA); fills of this slot:
+        const int64_t items = g > w ? (g - w + PIPE_A_WARPS - 1) / PIPE_A_WARPS : 0;
+        const int64_t fills = items > r ? (items - r + Cfg::RW - 1) / Cfg::RW : 0;
+        if (fills == 0) continue;
+        for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
+          if (sm103::mbar_try_wait(&full[slot], (uint32_t)((fills - 1) & 1))) break;
+      }
+    }
+  } else if (warp <= PIPE_A_WARPS) {
+    const int wa = warp - 1;
+    for (int64_t j = 0;; ++j) {
+      const int64_t g = wa + PIPE_A_WARPS * j;
+      const int64_t lt = g / 9;
+      const int s = (int)(g - lt * 9);
+      const int64_t tile = tile_begin + blockIdx.x + lt * gridDim.x;
+      if (tile >= tile_end) break;
+      const int slot = wa * Cfg::RW + (int)(j % Cfg::RW);
+      if (!sm103::mbar_wait(&full[slot], (uint32_t)((j / Cfg::RW) & 1), abort_flag)) {
+        give_up();
+        break;
+      }
+      const int zb = (int)(lt & 1);
+      if (lt >= 2 && !sm103::mbar_wait(&zempty[zb], (uint32_t)(((lt >> 1) - 1) & 1), abort_flag)) {
+        give_up();
+        break;
+      }
+      if (lane < 24) {
+        const int a3 = lane >> 3, olB = lane & 7;
+        const InT *src = ring + (size_t)slot * (Cfg::SUB_BYTES / sizeof(InT)) + a3 * 27 * 64 + olB * 8;
+        int32_t acc[64];
+#pragma unroll
+        for (int p = 0; p < 64; ++p) acc[p] = 0;
+#pragma unroll
+        for (int alA = 0; alA < 27; ++alA) {
+          int32_t v[8];
+          lds_row8<InT>(src + alA * 64, v);
+          wht<3>(v);
+#pragma unroll
+          for (int m = 0; m < 8; ++m) acc[block_pauli(alA, m, 3)] += v[m];
+        }
+        int32_t *z = Z + zb * Z_WORDS + s * 24 + lane;
+#pragma unroll
+        for (int p = 0; p < 64; ++p) z[p * P1_ZSTRIDE] = acc[p];
+      }
+      sm103::mbar_arrive(&empty[slot]);
+      sm103::mbar_arrive(&zfull[zb]);
+    }
+  } else {
+    const int tb = threadIdx.x - 32 * (PIPE_A_WARPS + 1);  // 0..63
+    for (int64_t lt = 0;; ++lt) {
+      const int64_t tile = tile_begin + blockIdx.x + lt * gridDim.x;
+      if (tile >= tile_end) break;
+      const int zb = (int)(lt & 1);
+      if (!sm103::mbar_wait(&zfull[zb], (uint32_t)((lt >> 1) & 1), abort_flag)) {
+        give_up();
+        break;
+      }
+      const int32_t *z = Z + zb * Z_WORDS + tb * P1_ZSTRIDE;
+      int32_t acc[64];
+#pragma unroll
+      for (int p = 0; p < 64; ++p) acc[p] = 0;
+#pragma unroll
+      for (int alB = 0; alB < 27; ++alB) {
+        int32_t v[8];
+#pragma unroll
+        for (int olB = 0; olB < 8; ++olB) v[olB] = z[alB * 8 + olB];
+        wht<3>(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
+      }
+      sm103::mbar_arrive(&zempty[zb]);
+      int32_t *o = out + tile * 4096 + tb;
+#pragma unroll
+      for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
+    }
+  }
+}
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// TMA map over rows [0, rows) of a [rows][2^n] count matrix, box 81 x 64.
+bool make_count_map(CUtensorMap *map, const void *base, lre_count_kind kind, int n, int64_t rows) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const size_t es = kind == LRE_COUNTS_I16 ? 2 : 4;
+  const cuuint64_t dims[2] = {(cuuint64_t)1 << n, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {((cuuint64_t)1 << n) * es};
+  const cuuint32_t box[2] = {64, SUB_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, kind == LRE_COUNTS_I16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_INT32,
+                   2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
 // Generic pass: one thread per (ah, oh, c) column, J <= 3 qubits in registers.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -178,7 +406,21 @@ struct GenParams {
   double shots;          // N (final uniform)
   int64_t total;         // N * 3^n (final uniform check)
   int *status;
+  int64_t *T;            // optional: exact integers S_i 3^(n-k) for the integer assembly
+  double denom[16];      // N 3^k (uniform) or 3^k (weighted), exact
+  double recip[16];      // correctly rounded 1 / denom[k]
+  int64_t up3[16];       // 3^(n-k)
 };
+
+// a / b correctly rounded, from y = RN(1/b): q = RN(a y) is within one ulp of
+// a/b, the residual a - b q is exact under FMA, and one more FMA gives the
+// correctly rounded quotient (Markstein; Muller et al., Handbook of
+// Floating-Point Arithmetic, the FMA-based division correction theorem).
+__device__ __forceinline__ double div_by_recip(double a, double b, double y) {
+  const double q = a * y;
+  const double r = fma(-q, b, a);
+  return fma(r, y, q);
+}
 
 template <int J, typename InT, typename AccT, int MODE, bool WEIGHT>
 __global__ void __launch_bounds__(256) fold_generic(GenParams P) {
@@ -233,9 +475,10 @@ __global__ void __launch_bounds__(256) fold_generic(GenParams P) {
         const int k = identity_letters((uint64_t)i, P.n);
         if constexpr (MODE == M_FINAL_U) {
           if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
-          out[i] = (double)acc[p] / (P.shots * pow3d(k));
+          out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
+          if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
         } else {
-          out[i] = (double)acc[p] / pow3d(k);
+          out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
         }
       }
     }
@@ -412,12 +655,30 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       out = (k % 2 == 0) ? bufA : bufB;
     else
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
-    if (pp.first6) {
+    CUtensorMap tmap;
+    if (pp.first6 && !ctx->legacy_first_pass &&
+        make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {
+      const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
+      int grid = ctx->num_sms;
+      if ((int64_t)grid > tiles) grid = (int)tiles;
+      Launch L(ctx, "fold_first6", s);
+      if (pp.in_t == T_I16) {
+        constexpr int sm = PipeCfg<int16_t>::SMEM;
+        cudaFuncSetAttribute(fold_first6_pipe<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        fold_first6_pipe<int16_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, static_cast<int32_t *>(out), pp.r, 0,
+                                                                 tiles, 0, ctx->d_status);
+      } else {
+        constexpr int sm = PipeCfg<int32_t>::SMEM;
+        cudaFuncSetAttribute(fold_first6_pipe<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        fold_first6_pipe<int32_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, static_cast<int32_t *>(out), pp.r, 0,
+                                                                 tiles, 0, ctx->d_status);
+      }
+    } else if (pp.first6) {
       const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
       const size_t smem = 64 * P1_ZSTRIDE * sizeof(int32_t);
       int grid = ctx->num_sms * 2;
       if ((int64_t)grid > tiles) grid = (int)tiles;
-      Launch L(ctx, "fold_first6", s);
+      Launch L(ctx, "fold_first6_regs", s);
       if (pp.in_t == T_I16) {
         cudaFuncSetAttribute(fold_first6<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         fold_first6<int16_t><<<grid, P1_THREADS, smem, s>>>(static_cast<const int16_t *>(in),
@@ -441,6 +702,13 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       gp.wgt = wgt;
       gp.shots = (double)a.shots_uniform;
       gp.total = a.shots_uniform * B;
+      gp.T = a.T;
+      for (int k = 0; k < 16; ++k) {
+        const double p3 = (double)ipow(3, k <= a.n ? k : 0);
+        gp.denom[k] = weighted ? p3 : (double)a.shots_uniform * p3;  // exact: < 2^53
+        gp.recip[k] = 1.0 / gp.denom[k];                              // host IEEE division
+        gp.up3[k] = k <= a.n ? ipow(3, a.n - k) : 0;
+      }
       gp.status = ctx->d_status;
       int64_t blocks = (gp.items + 255) / 256;
       const int64_t cap = (int64_t)ctx->num_sms * 64;
@@ -456,3 +724,40 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
 }
 
 }  // namespace lre
+
+// Test hook (not part of include/lre.h): run only the 6-qubit first pass of
+// step (i) over all tiles, variant 0 = register-only kernel, 1 = TMA
+// pipeline.  out: device int32 [3^(n-6)][2^(n-6)][4096].
+extern "C" lre_status lre_debug_first_pass(lre_ctx *ctx, const void *counts, lre_count_kind kind, int n,
+                                           int32_t *out, int variant, lre_stream stream) {
+  using namespace lre;
+  if (!ctx || !counts || !out || n < 7 || n > 14) return LRE_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t tiles = ipow(3, n - 6) << (n - 6);
+  if (variant == 1) {
+    CUtensorMap tmap;
+    if (!make_count_map(&tmap, counts, kind, n, ipow(3, n))) return LRE_ERR_CUDA;
+    const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
+    if (kind == LRE_COUNTS_I16) {
+      constexpr int sm = PipeCfg<int16_t>::SMEM;
+      cudaFuncSetAttribute(fold_first6_pipe<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      fold_first6_pipe<int16_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, out, n, 0, tiles, 0, ctx->d_status);
+    } else {
+      constexpr int sm = PipeCfg<int32_t>::SMEM;
+      cudaFuncSetAttribute(fold_first6_pipe<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      fold_first6_pipe<int32_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, out, n, 0, tiles, 0, ctx->d_status);
+    }
+  } else {
+    const size_t smem = 64 * P1_ZSTRIDE * sizeof(int32_t);
+    const int grid = (int)(tiles < 2 * ctx->num_sms ? tiles : 2 * ctx->num_sms);
+    if (kind == LRE_COUNTS_I16) {
+      cudaFuncSetAttribute(fold_first6<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      fold_first6<int16_t><<<grid, P1_THREADS, smem, s>>>(static_cast<const int16_t *>(counts), out, n, tiles);
+    } else {
+      cudaFuncSetAttribute(fold_first6<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      fold_first6<int32_t><<<grid, P1_THREADS, smem, s>>>(static_cast<const int32_t *>(counts), out, n, tiles);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "debug first pass");
+}

@@ -38,8 +38,9 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
   const size_t fold_ws = fold_workspace_bytes(n, ck, false, shots);
   const size_t asm_ws = rho_host ? assemble_workspace_bytes(n) : 0;
   const size_t dev_ws = up256(fold_ws > asm_ws ? fold_ws : asm_ws);
+  const size_t t_bytes = rho_host ? up256((size_t)ipow(4, n) * sizeof(int64_t)) : 0;
   const size_t need = dev_ws + up256(counts_bytes) + up256(theta_bytes) + up256(rho_bytes) +
-                      (records ? 2 * up256(chunk_in) : 0);
+                      (records ? 2 * up256(chunk_in) : 0) + t_bytes;
   lre_status st = ensure_workspace(ctx, need);
   if (st != LRE_OK) return st;
   char *p = static_cast<char *>(ctx->ws);
@@ -47,8 +48,9 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
   char *counts = p + dev_ws;
   double *theta = reinterpret_cast<double *>(counts + up256(counts_bytes));
   lre_c64 *rho = reinterpret_cast<lre_c64 *>(reinterpret_cast<char *>(theta) + up256(theta_bytes));
-  char *stage[2] = {reinterpret_cast<char *>(rho) + up256(rho_bytes), nullptr};
-  stage[1] = stage[0] + up256(chunk_in);
+  char *tail = reinterpret_cast<char *>(rho) + up256(rho_bytes);
+  int64_t *T = rho_host ? reinterpret_cast<int64_t *>(tail) : nullptr;
+  char *stage[2] = {tail + t_bytes, tail + t_bytes + up256(chunk_in)};  // records only
 
   cudaError_t e = cudaSuccess;
   if (!ctx->copy_stream) {
@@ -82,8 +84,9 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host input streaming");
   FoldArgs fa{counts, ck, n, nullptr, shots, theta, nullptr};
+  fa.T = T;
   if ((st = fold_run(ctx, fa, ws, dev_ws, s)) != LRE_OK) return st;
-  if (rho_host && (st = assemble_run(ctx, theta, n, rho, ws, s)) != LRE_OK) return st;
+  if (rho_host && (st = assemble_int_run(ctx, T, n, shots, rho, ws, s)) != LRE_OK) return st;
   e = cudaMemcpyAsync(theta_host, theta, theta_bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && rho_host) e = cudaMemcpyAsync(rho_host, rho, rho_bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -31,6 +31,7 @@ struct lre_ctx {
   std::vector<lre_prof_entry> prof_pool;  // reused events
   size_t prof_used = 0;
   uint64_t launches = 0;                  // kernels of this library launched so far
+  bool legacy_first_pass = false;         // use the register-only first pass (A/B tests)
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
@@ -74,6 +75,7 @@ struct FoldArgs {
   int64_t shots_uniform;  // used when shots == nullptr
   double *theta;          // final FP64 output (estimate mode) or nullptr
   int64_t *S;             // final int64 output (parity-sum mode) or nullptr
+  int64_t *T = nullptr;   // optional exact integers S_i 3^(n-k_i) (uniform shots)
 };
 size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound);
 lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s);
@@ -82,6 +84,9 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
 size_t assemble_workspace_bytes(int n);
 lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
                         cudaStream_t s);
+// Exact-integer variant for uniform shots: T_i = S_i 3^(n-k_i) (= t_i N 3^n).
+lre_status assemble_int_run(lre_ctx *ctx, const int64_t *T, int n, int64_t shots, lre_c64 *rho,
+                            void *ws, cudaStream_t s);
 
 // ---- step (iii): rho -> physical rho ----------------------------------------
 lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,

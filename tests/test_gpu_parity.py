@@ -207,3 +207,25 @@ def test_estimate_host_matches_device_path(env, n, kind):
     t_ref = direct.estimate(counts, N, n)
     np.testing.assert_array_equal(th.numpy(), t_ref)
     assert rel_fro(rh.numpy(), direct.mu(t_ref, n)) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [10, 11, 12, 13])
+def test_assemble_tiled_passes_sampled(env, n):
+    """n >= 10 uses the shared-memory tiled passes (6 + 4 + ... qubits)."""
+    torch, lre, ctx = env
+    rng = np.random.default_rng(500 + n)
+    t = rng.uniform(-1, 1, 4 ** n)
+    t[0] = 1.0
+    d = 2 ** n
+    rho = torch.empty((d, d), dtype=torch.complex64, device="cuda")
+    lre.lre_assemble(ctx, torch.from_numpy(t).cuda(), n, rho)
+    lre.lre_sync(ctx)
+    r = rng.integers(0, d, 300)
+    c = rng.integers(0, d, 300)
+    r[:20] = c[:20]                                   # include diagonal elements
+    ref = direct.mu_elements(t, n, r, c)
+    got = rho[torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()].cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
+    tr = torch.diagonal(rho).sum().item()
+    assert abs(tr - 1) < 1e-4
+    assert torch.equal(rho, rho.conj().T)             # exactly Hermitian
