@@ -68,12 +68,6 @@ __device__ __forceinline__ int identity_letters(uint64_t i, int n) {
   return n - __popcll(nz & mask);
 }
 
-__device__ __forceinline__ double pow3d(int k) {
-  double r = 1.0;
-  for (int q = 0; q < k; ++q) r *= 3.0;
-  return r;
-}
-
 // ---------------------------------------------------------------------------
 // Two-level first pass over the raw counts: 6 qubits per tile.
 //   tile = (ah, oh): 729 basis rows x 64 consecutive outcomes.
@@ -387,13 +381,6 @@ bool make_count_map(CUtensorMap *map, const void *base, lre_count_kind kind, int
 // ---------------------------------------------------------------------------
 // Generic pass: one thread per (ah, oh, c) column, J <= 3 qubits in registers.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct Ty;
-template <> struct Ty<int16_t> { static constexpr int id = T_I16; };
-template <> struct Ty<int32_t> { static constexpr int id = T_I32; };
-template <> struct Ty<int64_t> { static constexpr int id = T_I64; };
-template <> struct Ty<double> { static constexpr int id = T_F64; };
-
 struct GenParams {
   const void *in;
   void *out;
