@@ -124,6 +124,20 @@ lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, c
  * rho: device complex64 [2^n][2^n]. */
 lre_status lre_assemble(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, lre_stream stream);
 
+/* Step (ii) for callers that cannot allocate device memory (the paper has
+ * no counterpart: this is a deployment variant of lre_assemble).  Same
+ * arguments, result and FP64 arithmetic as lre_assemble, but no context and
+ * no allocation: the FP64 scratch of the butterfly passes is a fixed 32 MiB
+ * array in the library's device image, which every GPU that loads the
+ * library holds until the process exits.  Runs on the calling thread's
+ * current device, on `stream`.  1 <= n <= 10; a larger n returns
+ * LRE_ERR_UNSUPPORTED (the scratch would not fit) and enqueues nothing.
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture).  All calls share the array: calls that
+ * overlap on the GPU race on it and must be serialised by the caller.  No
+ * part of the array needs to start at zero. */
+lre_status lre_assemble_noalloc(const double *theta, int n, lre_c64 *rho, lre_stream stream);
+
 /* Step (iii): rho_out = argmin over density matrices sigma of
  * ||sigma - rho_in||_F (Sec. II, Smolin et al.): FP64 Hermitian
  * eigendecomposition of rho_in (promoted to complex128), the eigenvalue

@@ -40,6 +40,7 @@ SIGNATURES = [
     ("lre_parity_sums", _i, [_p, _p, _i, _i, _i64, _p, _p]),
     ("lre_estimate", _i, [_p, _p, _i, _p, _i64, _i, _p, _p, _p]),
     ("lre_assemble", _i, [_p, _p, _i, _p, _p]),
+    ("lre_assemble_noalloc", _i, [_p, _i, _p, _p]),
     ("lre_project", _i, [_p, _p, _i, _p, _p, _p, _p]),
     ("lre_histogram", _i, [_p, _p, _i64, _i64, _i, _p, _i, _p]),
     ("lre_estimate_host", _i, [_p, _p, _i, _i64, _i, _p, _p, _p]),
@@ -148,6 +149,11 @@ def lre_estimate(ctx, counts, shots, n, theta, rho=None, stream=None):
 
 def lre_assemble(ctx, theta, n, rho, stream=None):
     _check(load().lre_assemble(ctx, _ptr(theta), int(n), _ptr(rho), _stream(stream)), ctx)
+
+
+def lre_assemble_noalloc(theta, n, rho, stream=None):
+    """Step (ii) without any device allocation (fixed 32 MiB scratch, n <= 10)."""
+    _check(load().lre_assemble_noalloc(_ptr(theta), int(n), _ptr(rho), _stream(stream)))
 
 
 def lre_project(ctx, rho_in, n, rho_out, eig_mu=None, eig_rho=None, stream=None):
