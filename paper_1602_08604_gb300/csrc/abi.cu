@@ -185,7 +185,7 @@ lre_status lre_workspace_size(lre_ctx *ctx, int n, lre_count_kind kind, int per_
   lre_status st = check_n(n);
   if (st != LRE_OK) return st;
   if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
-  const size_t f = fold_workspace_bytes(n, kind, per_basis_shots != 0, per_basis_shots ? 0 : 1);
+  const size_t f = fold_workspace_bytes(n, kind, per_basis_shots != 0, per_basis_shots ? 0 : 1, ctx->first_variant);
   const size_t a = assemble_workspace_bytes(n);
   *bytes = f > a ? f : a;
   return LRE_OK;
@@ -199,7 +199,7 @@ lre_status lre_parity_sums(lre_ctx *ctx, const void *counts, lre_count_kind kind
   if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
   if ((st = set_device(ctx)) != LRE_OK) return st;
   // Without a bound every partial sum is int64.
-  const size_t need = fold_workspace_bytes(n, kind, false, row_total_bound);
+  const size_t need = fold_workspace_bytes(n, kind, false, row_total_bound, ctx->first_variant);
   if ((st = ensure_workspace(ctx, need)) != LRE_OK) return st;
   FoldArgs a{counts, kind, n, nullptr, row_total_bound, nullptr, S};
   return fold_run(ctx, a, ctx->ws, ctx->ws_bytes, reinterpret_cast<cudaStream_t>(stream));
@@ -214,7 +214,7 @@ lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, c
   if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
   if (!shots && shots_uniform <= 0) return LRE_ERR_INVALID_ARG;
   if ((st = set_device(ctx)) != LRE_OK) return st;
-  const size_t f = fold_workspace_bytes(n, kind, shots != nullptr, shots ? 0 : shots_uniform);
+  const size_t f = fold_workspace_bytes(n, kind, shots != nullptr, shots ? 0 : shots_uniform, ctx->first_variant);
   const size_t a = rho ? assemble_workspace_bytes(n) : 0;
   const size_t shared = f > a ? f : a;
   // uniform shots: rho is assembled from the exact integers T = S 3^(n-k)
@@ -329,3 +329,12 @@ lre_status lre_profile_get(lre_ctx *ctx, int i, const char **name, float *ms) {
 uint64_t lre_launch_count(lre_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 }  // extern "C"
+
+// Test hook (not part of include/lre.h): choose the first fold pass of later
+// calls on this context: 0 register kernel, 1 TMA pipeline, 2 TMA pipeline
+// fused with the second pass where the plan allows (the default).
+extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
+  if (!ctx || variant < 0 || variant > 2) return LRE_ERR_INVALID_ARG;
+  ctx->first_variant = variant;
+  return LRE_OK;
+}

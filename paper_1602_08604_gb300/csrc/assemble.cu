@@ -20,63 +20,23 @@
 // Layout after t qubits are done: [P_hi in 4^(n-t)][R_lo in 2^t][C_lo in 2^t],
 // so the final layout (t = n) is rho[R][C].  For n >= 10 the passes are
 // shared-memory tiled (6 qubits, then 4 at a time); smaller n and the
-// leftover qubits use register passes of 1-2 qubits.
+// leftover qubits use register passes of 1-2 qubits (passes.cuh).
 #include <cuda_runtime.h>
 
 #include "lre_internal.cuh"
+#include "passes.cuh"
 
 namespace lre {
 namespace {
 
-struct NumF64 {
-  using V = double2;
-  using In = double;
-};
-struct NumI64 {
-  using V = longlong2;
-  using In = long long;
-};
+using namespace passes;
 
-struct LastScale {
-  float sh, sl;  // 1/(2^n N 3^n) = sh + sl (integer path only)
-};
-
-__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-__device__ __forceinline__ longlong2 mk(long long a, long long b) { return make_longlong2(a, b); }
-
-// One qubit of the butterfly on (I, X, Y, Z) -> (00, 01, 10, 11).
-//   -i*Y = (Y.y, -Y.x);  +i*Y = (-Y.y, Y.x)
-__device__ __forceinline__ void m_qubit(double2 vI, double2 vX, double2 vY, double2 vZ, double2 &o00,
-                                        double2 &o01, double2 &o10, double2 &o11) {
-  o00 = mk(0.5 * (vI.x + vZ.x), 0.5 * (vI.y + vZ.y));
-  o11 = mk(0.5 * (vI.x - vZ.x), 0.5 * (vI.y - vZ.y));
-  o01 = mk(0.5 * (vX.x + vY.y), 0.5 * (vX.y - vY.x));
-  o10 = mk(0.5 * (vX.x - vY.y), 0.5 * (vX.y + vY.x));
-}
-__device__ __forceinline__ void m_qubit(longlong2 vI, longlong2 vX, longlong2 vY, longlong2 vZ,
-                                        longlong2 &o00, longlong2 &o01, longlong2 &o10, longlong2 &o11) {
-  o00 = mk(vI.x + vZ.x, vI.y + vZ.y);
-  o11 = mk(vI.x - vZ.x, vI.y - vZ.y);
-  o01 = mk(vX.x + vY.y, vX.y - vY.x);
-  o10 = mk(vX.x - vY.y, vX.y + vY.x);
-}
-
-__device__ __forceinline__ double2 load_first(const double *in, int64_t i) { return mk(__ldg(in + i), 0.0); }
-__device__ __forceinline__ longlong2 load_first(const long long *in, int64_t i) {
-  return mk(__ldg(in + i), 0ll);
-}
-
-// int64 -> float of v * (sh + sl), error about half an ulp of the float
-__device__ __forceinline__ float scaled(long long v, const LastScale &s) {
-  const float vh = (float)v;
-  const float vl = (float)(v - (long long)vh);
-  return __fmaf_rn(vh, s.sh, __fmaf_rn(vh, s.sl, vl * s.sh));
-}
-__device__ __forceinline__ float2 to_c64(double2 v, const LastScale &) {
-  return make_float2((float)v.x, (float)v.y);
-}
-__device__ __forceinline__ float2 to_c64(longlong2 v, const LastScale &s) {
-  return make_float2(scaled(v.x, s), scaled(v.y, s));
+// Register pass over J <= 2 qubits: one thread per (P', R_lo, C_lo).
+template <class Num, int J, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
+  for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < P.items;
+       item += (int64_t)gridDim.x * blockDim.x)
+    asm_item<Num, J, FIRST, LAST>(P, item);
 }
 
 template <typename V>
@@ -92,77 +52,6 @@ __device__ __forceinline__ void m2(V (&v)[16]) {
     V a, b, c, d;
     m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
     v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
-  }
-}
-
-struct AsmParams {
-  const void *in;
-  void *out;
-  int t;          // qubits already transformed
-  int n;
-  int64_t items;  // 4^(n-t-J) * 4^t
-  LastScale scale;
-};
-
-// Register pass over J <= 2 qubits: one thread per (P', R_lo, C_lo).
-template <class Num, int J, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
-  using V = typename Num::V;
-  constexpr int NP = 1 << (2 * J);
-  const int t = P.t;
-  const int tp = t + J;
-  const int64_t L4 = 1ll << (2 * t);  // 4^t
-  for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < P.items;
-       item += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t L = item & (L4 - 1);
-    const int64_t Pp = item >> (2 * t);
-    const int64_t R_lo = L >> t, C_lo = L & ((1ll << t) - 1);
-    V v[NP];
-    const int64_t ibase = Pp * NP * L4 + L;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if constexpr (FIRST)
-        v[p] = load_first(static_cast<const typename Num::In *>(P.in), ibase + p * L4);
-      else
-        v[p] = static_cast<const V *>(P.in)[ibase + p * L4];
-    }
-    // digit 0 (qubit t): index p = p1*4 + p0 -> u0 = 2 r0 + c0
-#pragma unroll
-    for (int h = 0; h < NP / 4; ++h) {
-      V a, b, c, d;
-      m_qubit(v[4 * h + 0], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3], a, b, c, d);
-      v[4 * h + 0] = a; v[4 * h + 1] = b; v[4 * h + 2] = c; v[4 * h + 3] = d;
-    }
-    if constexpr (J == 2) {
-#pragma unroll
-      for (int u0 = 0; u0 < 4; ++u0) {
-        V a, b, c, d;
-        m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
-        v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
-      }
-    }
-    // v[u1*4 + u0] with u_q = 2 r_q + c_q  ->  rj, cj
-    const int64_t W = 1ll << tp;
-    const int64_t obase = Pp * W * W;
-#pragma unroll
-    for (int u = 0; u < NP; ++u) {
-      int rj, cj;
-      if constexpr (J == 1) {
-        rj = u >> 1;
-        cj = u & 1;
-      } else {
-        const int u0 = u & 3, u1 = u >> 2;
-        rj = ((u1 >> 1) << 1) | (u0 >> 1);
-        cj = ((u1 & 1) << 1) | (u0 & 1);
-      }
-      const int64_t R = ((int64_t)rj << t) | R_lo;
-      const int64_t Cc = ((int64_t)cj << t) | C_lo;
-      const int64_t o = obase + R * W + Cc;
-      if constexpr (LAST)
-        static_cast<float2 *>(P.out)[o] = to_c64(v[u], P.scale);
-      else
-        static_cast<V *>(P.out)[o] = v[u];
-    }
   }
 }
 
@@ -362,6 +251,15 @@ size_t assemble_workspace_bytes(int n) {
   return 2 * ((one + 255) & ~(size_t)255);
 }
 
+LastScaleArgs int_assembly_scale(int n, int64_t shots) {
+  // 1 / (2^n N 3^n) split into two floats
+  const double scale = 1.0 / ((double)(1ll << n) * (double)shots * (double)ipow(3, n));
+  LastScaleArgs ls;
+  ls.sh = (float)scale;
+  ls.sl = (float)(scale - (double)ls.sh);
+  return ls;
+}
+
 lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
                         cudaStream_t s) {
   return run_passes<NumF64>(ctx, theta, n, rho, ws, LastScale{0.f, 0.f}, s);
@@ -369,12 +267,8 @@ lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
 
 lre_status assemble_int_run(lre_ctx *ctx, const int64_t *T, int n, int64_t shots, lre_c64 *rho,
                             void *ws, cudaStream_t s) {
-  // 1 / (2^n N 3^n) split into two floats
-  const double scale = 1.0 / ((double)(1ll << n) * (double)shots * (double)ipow(3, n));
-  LastScale ls;
-  ls.sh = (float)scale;
-  ls.sl = (float)(scale - (double)ls.sh);
-  return run_passes<NumI64>(ctx, reinterpret_cast<const long long *>(T), n, rho, ws, ls, s);
+  const LastScaleArgs a = int_assembly_scale(n, shots);
+  return run_passes<NumI64>(ctx, reinterpret_cast<const long long *>(T), n, rho, ws, LastScale{a.sh, a.sl}, s);
 }
 
 }  // namespace lre

@@ -27,46 +27,13 @@
 #include <vector>
 
 #include "lre_internal.cuh"
+#include "passes.cuh"
 #include "sm103.cuh"
 
 namespace lre {
 namespace {
 
-enum { T_I16 = 0, T_I32 = 1, T_I64 = 2, T_F64 = 3 };
-enum { M_STORE = 0, M_FINAL_U = 1, M_FINAL_W = 2, M_PARITY = 3 };
-
-// Pauli-digit index of the pass block: digit q is m_q ? a_q + 1 : 0 (a_q the
-// q-th ternary digit of al, m_q the q-th bit of the parity mask).
-__host__ __device__ constexpr int block_pauli(int al, int m, int J) {
-  int pl = 0, w = 1;
-  for (int q = 0; q < J; ++q) {
-    pl += (((m >> q) & 1) ? (al % 3) + 1 : 0) * w;
-    al /= 3;
-    w *= 4;
-  }
-  return pl;
-}
-
-template <int J, typename V>
-__device__ __forceinline__ void wht(V (&v)[1 << J]) {
-#pragma unroll
-  for (int h = 1; h < (1 << J); h <<= 1) {
-#pragma unroll
-    for (int i = 0; i < (1 << J); ++i) {
-      if ((i & h) == 0) {
-        V a = v[i], b = v[i + h];
-        v[i] = a + b;
-        v[i + h] = a - b;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ int identity_letters(uint64_t i, int n) {
-  uint64_t nz = (i | (i >> 1)) & 0x5555555555555555ull;
-  uint64_t mask = (n >= 32) ? ~0ull : ((1ull << (2 * n)) - 1);
-  return n - __popcll(nz & mask);
-}
+using namespace passes;
 
 // ---------------------------------------------------------------------------
 // Two-level first pass over the raw counts: 6 qubits per tile.
@@ -186,6 +153,57 @@ struct PipeCfg {
   static constexpr int SMEM = BAR_OFF + (2 * R + 4) * 8 + 16 + 1024;  // + alignment slack
 };
 
+// Fused first + second pass (6 + 3 qubits): first-pass tiles are processed
+// group-major, a group being the 27 x 8 tiles (qubits 6..8 of the a-digits
+// and o-bits) that one second-pass column reads; tile outputs go to a ring of
+// FUSE_RING group slots that stays in L2 and is read back by 32-column jobs
+// of two extra warps per CTA once the group's tile counter is complete.
+constexpr int FUSE_RING = 8;
+constexpr int FUSE_JOBS = 4096 / 32;  // second-pass jobs per group
+constexpr int FUSE_THREADS = PIPE_THREADS + 64;
+
+struct FuseState {  // zeroed before each launch; counters only grow
+  unsigned int job_next;
+  unsigned int tiles_done[FUSE_RING];
+  unsigned int jobs_done[FUSE_RING];
+};
+
+struct PipeArgs {
+  int32_t *out;      // first pass: [tiles][4096]; fused: second-pass output [groups][64][4096]
+  int32_t *scratch;  // fused: [FUSE_RING][216][4096]
+  FuseState *fs;     // fused
+  int fuse;
+  int n;
+  int64_t tile_begin, tile_end, row_base;
+  int *status;
+};
+
+__device__ __forceinline__ void tile_coords(int fuse, int64_t q, int64_t n_oh, int64_t &ah, int64_t &oh) {
+  if (!fuse) {
+    ah = q / n_oh;
+    oh = q - ah * n_oh;
+    return;
+  }
+  const int64_t G = q / 216, k = q - G * 216, n_goh = n_oh >> 3;
+  const int64_t gah = G / n_goh, goh = G - gah * n_goh;
+  ah = gah * 27 + k / 8;
+  oh = goh * 8 + (k & 7);
+}
+
+// Wait (bounded by time) until *p >= target; acquire ordering.
+__device__ __forceinline__ bool poll_at_least(unsigned int *p, unsigned int target, volatile int *abort) {
+  const uint64_t t0 = sm103::globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    if (v >= target) return true;
+    if ((it & 63u) == 63u) {
+      if (*abort || sm103::globaltimer() - t0 > sm103::kWaitNs) return false;
+      __nanosleep(64);
+    }
+  }
+}
+
 template <typename InT>
 __device__ __forceinline__ void lds_row8(const InT *p, int32_t (&v)[8]);
 
@@ -209,9 +227,12 @@ __device__ __forceinline__ void lds_row8<int32_t>(const int32_t *p, int32_t (&v)
 }
 
 template <typename InT>
-__global__ void __launch_bounds__(PIPE_THREADS, 1)
-    fold_first6_pipe(const __grid_constant__ CUtensorMap tmap, int32_t *__restrict__ out, int n,
-                     int64_t tile_begin, int64_t tile_end, int64_t row_base, int *status) {
+__global__ void __launch_bounds__(FUSE_THREADS, 1)
+    fold_first6_pipe(const __grid_constant__ CUtensorMap tmap, PipeArgs A) {
+  int32_t *__restrict__ out = A.out;
+  const int n = A.n;
+  const int64_t tile_begin = A.tile_begin, tile_end = A.tile_end, row_base = A.row_base;
+  int *status = A.status;
   using Cfg = PipeCfg<InT>;
   constexpr int R = Cfg::R;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -250,7 +271,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1)
       // w*RW + j % RW, fill f = j / RW of that slot
       int64_t g = 0;
       for (int64_t tile = tile_begin + blockIdx.x; tile < tile_end && !*abort_flag; tile += gridDim.x) {
-        const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
+        int64_t ah, oh;
+        tile_coords(A.fuse, tile, n_oh, ah, oh);
         for (int s = 0; s < 9; ++s, ++g) {
           const int w = (int)(g % PIPE_A_WARPS);
           const int64_t j = g / PIPE_A_WARPS;
@@ -316,7 +338,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1)
       sm103::mbar_arrive(&empty[slot]);
       sm103::mbar_arrive(&zfull[zb]);
     }
-  } else {
+  } else if (warp < PIPE_A_WARPS + 3) {
     const int tb = threadIdx.x - 32 * (PIPE_A_WARPS + 1);  // 0..63
     for (int64_t lt = 0;; ++lt) {
       const int64_t tile = tile_begin + blockIdx.x + lt * gridDim.x;
@@ -325,6 +347,20 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1)
       if (!sm103::mbar_wait(&zfull[zb], (uint32_t)((lt >> 1) & 1), abort_flag)) {
         give_up();
         break;
+      }
+      int32_t *dst = out + tile * 4096;
+      int slot = 0;
+      if (A.fuse) {
+        // ring slot of this tile's group; wait until the slot's previous group
+        // has been read by all of its second-pass jobs
+        const int64_t G = tile / 216;
+        slot = (int)(G % FUSE_RING);
+        const uint32_t need = (uint32_t)(FUSE_JOBS * (G / FUSE_RING));
+        if (need && !poll_at_least(&A.fs->jobs_done[slot], need, abort_flag)) {
+          give_up();
+          break;
+        }
+        dst = A.scratch + ((int64_t)slot * 216 + (tile - G * 216)) * 4096;
       }
       const int32_t *z = Z + zb * Z_WORDS + tb * P1_ZSTRIDE;
       int32_t acc[64];
@@ -340,9 +376,59 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1)
         for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
       }
       sm103::mbar_arrive(&zempty[zb]);
-      int32_t *o = out + tile * 4096 + tb;
+      int32_t *o = dst + tb;
+      if (A.fuse) {
 #pragma unroll
-      for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
+        for (int p = 0; p < 64; ++p) o[p * 64] = acc[p];  // stays in L2 for the second pass
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(&A.fs->tiles_done[slot], 1u);  // one count per level-B warp
+      } else {
+#pragma unroll
+        for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
+      }
+    }
+  } else if (A.fuse) {
+    // second pass (qubits 6..8) over finished groups, one 32-column job per
+    // warp: input the group's 216 tile outputs (27 a-digit x 8 o-bit
+    // combinations) from L2, output [G][64][4096] like fold_generic<3>.
+    const int64_t total_jobs = (int64_t)((tile_end - tile_begin) / 216) * FUSE_JOBS;
+    for (;;) {
+      uint32_t jj = 0;
+      if (lane == 0) jj = atomicAdd(&A.fs->job_next, 1u);
+      const int64_t j = __shfl_sync(0xffffffffu, jj, 0);
+      if (j >= total_jobs || *abort_flag) break;
+      const int64_t G = j / FUSE_JOBS;
+      const int chunk = (int)(j - G * FUSE_JOBS);
+      const int slot = (int)(G % FUSE_RING);
+      if (!poll_at_least(&A.fs->tiles_done[slot], (uint32_t)(2 * 216 * (G / FUSE_RING + 1)), abort_flag)) {
+        give_up();
+        break;
+      }
+      const int32_t *src = A.scratch + (int64_t)slot * 216 * 4096 + chunk * 32 + lane;
+      int32_t acc[64];
+#pragma unroll
+      for (int p = 0; p < 64; ++p) acc[p] = 0;
+#pragma unroll
+      for (int al2 = 0; al2 < 27; ++al2) {
+        int32_t v[8];
+#pragma unroll
+        for (int ol2 = 0; ol2 < 8; ++ol2) v[ol2] = __ldcg(src + (al2 * 8 + ol2) * 4096);
+        wht<3>(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[block_pauli(al2, m, 3)] += v[m];
+      }
+      int32_t *o = A.out + (G - tile_begin / 216) * 64 * 4096 + chunk * 32 + lane;
+#pragma unroll
+      for (int p = 0; p < 64; ++p) __stcs(o + p * 4096, acc[p]);
+      __syncwarp();
+      // the 216 consumed 128-byte lines are dead: drop them from L2 unwritten
+      const int32_t *line0 = A.scratch + (int64_t)slot * 216 * 4096 + chunk * 32;
+      for (int r = lane; r < 216; r += 32)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(line0 + r * 4096) : "memory");
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicAdd(&A.fs->jobs_done[slot], 1u);
     }
   }
 }
@@ -381,95 +467,12 @@ bool make_count_map(CUtensorMap *map, const void *base, lre_count_kind kind, int
 // ---------------------------------------------------------------------------
 // Generic pass: one thread per (ah, oh, c) column, J <= 3 qubits in registers.
 // ---------------------------------------------------------------------------
-struct GenParams {
-  const void *in;
-  void *out;
-  int64_t C;       // columns already produced (4^(n-r))
-  int64_t n_oh;    // 2^(r-J)
-  int64_t items;   // 3^(r-J) * 2^(r-J) * C
-  int r;           // qubits left before this pass
-  int n;
-  const double *wgt;     // 1/N_b per basis (weighted first pass)
-  double shots;          // N (final uniform)
-  int64_t total;         // N * 3^n (final uniform check)
-  int *status;
-  int64_t *T;            // optional: exact integers S_i 3^(n-k) for the integer assembly
-  double denom[16];      // N 3^k (uniform) or 3^k (weighted), exact
-  double recip[16];      // correctly rounded 1 / denom[k]
-  int64_t up3[16];       // 3^(n-k)
-};
-
-// a / b correctly rounded, from y = RN(1/b): q = RN(a y) is within one ulp of
-// a/b, the residual a - b q is exact under FMA, and one more FMA gives the
-// correctly rounded quotient (Markstein; Muller et al., Handbook of
-// Floating-Point Arithmetic, the FMA-based division correction theorem).
-__device__ __forceinline__ double div_by_recip(double a, double b, double y) {
-  const double q = a * y;
-  const double r = fma(-q, b, a);
-  return fma(r, y, q);
-}
-
+// Generic pass: one thread per (ah, oh, c) column, J <= 3 qubits in registers.
 template <int J, typename InT, typename AccT, int MODE, bool WEIGHT>
 __global__ void __launch_bounds__(256) fold_generic(GenParams P) {
-  constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
-  constexpr int NO = 1 << J;
-  constexpr int NP = 1 << (2 * J);
-  const InT *__restrict__ in = static_cast<const InT *>(P.in);
-  const int64_t row_stride = (1ll << P.r) * P.C;  // al stride
   for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < P.items;
-       item += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = item % P.C;
-    const int64_t ahoh = item / P.C;
-    const int64_t oh = ahoh % P.n_oh;
-    const int64_t ah = ahoh / P.n_oh;
-    const int64_t base = ((ah * NA) << P.r) * P.C + (oh * NO) * P.C + c;
-    AccT acc[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) acc[p] = 0;
-#pragma unroll
-    for (int al = 0; al < NA; ++al) {
-      if constexpr (WEIGHT) {
-        int32_t v[NO];
-#pragma unroll
-        for (int ol = 0; ol < NO; ++ol) v[ol] = (int32_t)__ldg(in + base + al * row_stride + ol * P.C);
-        wht<J>(v);
-        const double w = __ldg(P.wgt + ah * NA + al);
-#pragma unroll
-        for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += (double)v[m] * w;
-      } else {
-        AccT v[NO];
-#pragma unroll
-        for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)__ldg(in + base + al * row_stride + ol * P.C);
-        wht<J>(v);
-#pragma unroll
-        for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
-      }
-    }
-    const int64_t obase = ahoh * NP * P.C + c;
-    if constexpr (MODE == M_STORE) {
-      AccT *out = static_cast<AccT *>(P.out);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) out[obase + p * P.C] = acc[p];
-    } else if constexpr (MODE == M_PARITY) {
-      int64_t *out = static_cast<int64_t *>(P.out);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) out[obase + p * P.C] = (int64_t)acc[p];
-    } else {
-      double *out = static_cast<double *>(P.out);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const int64_t i = obase + p * P.C;  // ahoh == 0 in the last pass
-        const int k = identity_letters((uint64_t)i, P.n);
-        if constexpr (MODE == M_FINAL_U) {
-          if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
-          out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
-          if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
-        } else {
-          out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
-        }
-      }
-    }
-  }
+       item += (int64_t)gridDim.x * blockDim.x)
+    fold_item<J, InT, AccT, MODE, WEIGHT>(P, item);
 }
 
 using GenKernel = void (*)(GenParams);
@@ -530,6 +533,7 @@ int type_size(int t) { return t == T_I16 ? 2 : (t == T_I32 ? 4 : 8); }
 
 struct PassPlan {
   bool first6;
+  bool fused9;  // first pass fused with the second through L2 (6 + 3 qubits)
   int J, r, in_t, acc_t, mode;
   bool weight;
   int64_t C;
@@ -539,7 +543,7 @@ struct PassPlan {
 // Build the pass schedule.  shots_bound: an upper bound on every basis' total
 // count (decides int32 vs int64 partial sums); weighted: FP64 path.
 std::vector<PassPlan> make_plan(int n, lre_count_kind kind, bool weighted, bool parity,
-                                int64_t shots_bound, bool aligned16) {
+                                int64_t shots_bound, bool aligned16, int variant) {
   std::vector<PassPlan> plan;
   int r = n, t = 0;
   int64_t C = 1;
@@ -547,7 +551,23 @@ std::vector<PassPlan> make_plan(int n, lre_count_kind kind, bool weighted, bool 
   auto fits32 = [&](int tt) {
     return shots_bound > 0 && (double)ipow(3, tt) * (double)shots_bound < 2147483647.0;
   };
-  if (!weighted && n >= 6 && r > 6 && aligned16 && fits32(6)) {
+  if (!weighted && r > 9 && aligned16 && fits32(9) && variant >= 2) {
+    PassPlan p{};
+    p.first6 = true;
+    p.fused9 = true;
+    p.J = 9;
+    p.r = r;
+    p.in_t = in_t;
+    p.acc_t = T_I32;
+    p.mode = M_STORE;
+    p.C = C;
+    p.out_bytes = (size_t)ipow(6, r - 9) * ((size_t)1 << 18) * 4;
+    plan.push_back(p);
+    r -= 9;
+    t += 9;
+    C <<= 18;
+    in_t = T_I32;
+  } else if (!weighted && n >= 6 && r > 6 && aligned16 && fits32(6)) {
     PassPlan p{};
     p.first6 = true;
     p.J = 6;
@@ -598,12 +618,20 @@ size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound) {
-  auto plan = make_plan(n, kind, weighted, false, shots_bound, true);
+constexpr size_t FUSE_SCRATCH_BYTES = (size_t)FUSE_RING * 216 * 4096 * 4;
+
+size_t fuse_bytes(const std::vector<PassPlan> &plan) {
+  for (const auto &pp : plan)
+    if (pp.fused9) return round_up(FUSE_SCRATCH_BYTES) + round_up(sizeof(FuseState));
+  return 0;
+}
+
+size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound, int variant) {
+  auto plan = make_plan(n, kind, weighted, false, shots_bound, true, variant);
   size_t a, b;
   plan_buffers(plan, a, b);
   size_t w = weighted ? round_up((size_t)ipow(3, n) * sizeof(double)) : 0;
-  return round_up(a) + round_up(b) + w;
+  return round_up(a) + round_up(b) + w + fuse_bytes(plan);
 }
 
 __global__ void inv_shots_kernel(const int64_t *shots, double *w, int64_t B, int *status) {
@@ -620,14 +648,18 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
   const bool parity = a.S != nullptr;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(a.counts) & 15) == 0;
   const int64_t bound = weighted ? 0 : a.shots_uniform;
-  auto plan = make_plan(a.n, a.kind, weighted, parity, bound, aligned16);
+  auto plan = make_plan(a.n, a.kind, weighted, parity, bound, aligned16, ctx->first_variant);
   size_t bA, bB;
   plan_buffers(plan, bA, bB);
   char *p = static_cast<char *>(ws);
   void *bufA = p;
   void *bufB = p + round_up(bA);
+  const size_t wbytes = weighted ? round_up((size_t)ipow(3, a.n) * 8) : 0;
   double *wgt = reinterpret_cast<double *>(p + round_up(bA) + round_up(bB));
-  const size_t need = round_up(bA) + round_up(bB) + (weighted ? round_up((size_t)ipow(3, a.n) * 8) : 0);
+  int32_t *fuse_scratch = reinterpret_cast<int32_t *>(p + round_up(bA) + round_up(bB) + wbytes);
+  FuseState *fuse_state = reinterpret_cast<FuseState *>(reinterpret_cast<char *>(fuse_scratch) +
+                                                         round_up(FUSE_SCRATCH_BYTES));
+  const size_t need = round_up(bA) + round_up(bB) + wbytes + fuse_bytes(plan);
   if (need > ws_bytes) return LRE_ERR_OOM;
   const int64_t B = ipow(3, a.n);
   if (weighted) {
@@ -643,24 +675,37 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
     else
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
     CUtensorMap tmap;
-    if (pp.first6 && !ctx->legacy_first_pass &&
+    if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
         make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {
       const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
       int grid = ctx->num_sms;
       if ((int64_t)grid > tiles) grid = (int)tiles;
-      Launch L(ctx, "fold_first6", s);
+      PipeArgs A{};
+      A.out = static_cast<int32_t *>(out);
+      A.n = pp.r;
+      A.tile_begin = 0;
+      A.tile_end = tiles;
+      A.row_base = 0;
+      A.status = ctx->d_status;
+      A.fuse = pp.fused9 ? 1 : 0;
+      const int threads = pp.fused9 ? FUSE_THREADS : PIPE_THREADS;
+      if (pp.fused9) {
+        A.scratch = fuse_scratch;
+        A.fs = fuse_state;
+        cudaError_t e0 = cudaMemsetAsync(fuse_state, 0, sizeof(FuseState), s);
+        if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "fused pass state");
+      }
+      Launch L(ctx, pp.fused9 ? "fold_first9_fused" : "fold_first6", s);
       if (pp.in_t == T_I16) {
         constexpr int sm = PipeCfg<int16_t>::SMEM;
         cudaFuncSetAttribute(fold_first6_pipe<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        fold_first6_pipe<int16_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, static_cast<int32_t *>(out), pp.r, 0,
-                                                                 tiles, 0, ctx->d_status);
+        fold_first6_pipe<int16_t><<<grid, threads, sm, s>>>(tmap, A);
       } else {
         constexpr int sm = PipeCfg<int32_t>::SMEM;
         cudaFuncSetAttribute(fold_first6_pipe<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        fold_first6_pipe<int32_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, static_cast<int32_t *>(out), pp.r, 0,
-                                                                 tiles, 0, ctx->d_status);
+        fold_first6_pipe<int32_t><<<grid, threads, sm, s>>>(tmap, A);
       }
-    } else if (pp.first6) {
+    } else if (pp.first6 && !pp.fused9) {
       const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
       const size_t smem = 64 * P1_ZSTRIDE * sizeof(int32_t);
       int grid = ctx->num_sms * 2;
@@ -725,14 +770,19 @@ extern "C" lre_status lre_debug_first_pass(lre_ctx *ctx, const void *counts, lre
     CUtensorMap tmap;
     if (!make_count_map(&tmap, counts, kind, n, ipow(3, n))) return LRE_ERR_CUDA;
     const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
+    PipeArgs A{};
+    A.out = out;
+    A.n = n;
+    A.tile_end = tiles;
+    A.status = ctx->d_status;
     if (kind == LRE_COUNTS_I16) {
       constexpr int sm = PipeCfg<int16_t>::SMEM;
       cudaFuncSetAttribute(fold_first6_pipe<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      fold_first6_pipe<int16_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, out, n, 0, tiles, 0, ctx->d_status);
+      fold_first6_pipe<int16_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, A);
     } else {
       constexpr int sm = PipeCfg<int32_t>::SMEM;
       cudaFuncSetAttribute(fold_first6_pipe<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      fold_first6_pipe<int32_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, out, n, 0, tiles, 0, ctx->d_status);
+      fold_first6_pipe<int32_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, A);
     }
   } else {
     const size_t smem = 64 * P1_ZSTRIDE * sizeof(int32_t);

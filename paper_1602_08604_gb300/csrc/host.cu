@@ -35,7 +35,7 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
   if (rows < 1) rows = 1;
   if (rows > B) rows = B;
   const size_t chunk_in = (size_t)rows * row_in;
-  const size_t fold_ws = fold_workspace_bytes(n, ck, false, shots);
+  const size_t fold_ws = fold_workspace_bytes(n, ck, false, shots, ctx->first_variant);
   const size_t asm_ws = rho_host ? assemble_workspace_bytes(n) : 0;
   const size_t dev_ws = up256(fold_ws > asm_ws ? fold_ws : asm_ws);
   const size_t t_bytes = rho_host ? up256((size_t)ipow(4, n) * sizeof(int64_t)) : 0;

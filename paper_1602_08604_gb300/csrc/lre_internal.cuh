@@ -31,7 +31,10 @@ struct lre_ctx {
   std::vector<lre_prof_entry> prof_pool;  // reused events
   size_t prof_used = 0;
   uint64_t launches = 0;                  // kernels of this library launched so far
-  bool legacy_first_pass = false;         // use the register-only first pass (A/B tests)
+  // first fold pass: 0 register kernel, 1 TMA pipeline (default), 2 TMA
+  // pipeline fused with the second pass through L2 (correct, but slower on
+  // GB300 so far: its second-pass jobs are L2-latency bound)
+  int first_variant = 1;
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
@@ -77,7 +80,8 @@ struct FoldArgs {
   int64_t *S;             // final int64 output (parity-sum mode) or nullptr
   int64_t *T = nullptr;   // optional exact integers S_i 3^(n-k_i) (uniform shots)
 };
-size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound);
+size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound,
+                            int variant = 2);
 lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s);
 
 // ---- step (ii): theta -> rho -------------------------------------------------
@@ -87,6 +91,10 @@ lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
 // Exact-integer variant for uniform shots: T_i = S_i 3^(n-k_i) (= t_i N 3^n).
 lre_status assemble_int_run(lre_ctx *ctx, const int64_t *T, int n, int64_t shots, lre_c64 *rho,
                             void *ws, cudaStream_t s);
+struct LastScaleArgs {
+  float sh, sl;  // 1/(2^n N 3^n) = sh + sl
+};
+LastScaleArgs int_assembly_scale(int n, int64_t shots);
 
 // ---- step (iii): rho -> physical rho ----------------------------------------
 lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,

@@ -1,0 +1,269 @@
+// Per-item bodies of the register-level passes of steps (i) and (ii), shared
+// by the standalone pass kernels (fold.cu, assemble.cu) and the batched
+// persistent kernel (batch.cu).
+//
+// Step (i) (Sec. III, Eq. 3): a pass contracts J qubits of the view
+//   X[ah][al][oh][ol][c] -> Y[ah][oh][pl][c]   (al in 3^J, ol in 2^J, pl in 4^J)
+// with the per-qubit map T (2-point WHT over the outcome bit, then I = sum
+// of the three axes, X/Y/Z = the matching axis); the last pass divides by
+// N 3^k (k identity letters) and can also emit T_i = S_i 3^(n-k).
+// Step (ii) (Eq. 4): a pass applies the per-qubit map (I,X,Y,Z) ->
+// (I+Z, X-iY, X+iY, I-Z) (times 1/2 in FP64; unscaled on exact integers) to
+// J qubits of [P_hi][R_lo][C_lo].
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lre_internal.cuh"
+
+namespace lre {
+namespace passes {
+
+enum { T_I16 = 0, T_I32 = 1, T_I64 = 2, T_F64 = 3 };
+enum { M_STORE = 0, M_FINAL_U = 1, M_FINAL_W = 2, M_PARITY = 3 };
+
+// Pauli-digit index of a pass block: digit q is m_q ? a_q + 1 : 0 (a_q the
+// q-th ternary digit of al, m_q the q-th bit of the parity mask).
+__host__ __device__ constexpr int block_pauli(int al, int m, int J) {
+  int pl = 0, w = 1;
+  for (int q = 0; q < J; ++q) {
+    pl += (((m >> q) & 1) ? (al % 3) + 1 : 0) * w;
+    al /= 3;
+    w *= 4;
+  }
+  return pl;
+}
+
+template <int J, typename V>
+__device__ __forceinline__ void wht(V (&v)[1 << J]) {
+#pragma unroll
+  for (int h = 1; h < (1 << J); h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < (1 << J); ++i) {
+      if ((i & h) == 0) {
+        V a = v[i], b = v[i + h];
+        v[i] = a + b;
+        v[i + h] = a - b;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int identity_letters(uint64_t i, int n) {
+  uint64_t nz = (i | (i >> 1)) & 0x5555555555555555ull;
+  uint64_t mask = (n >= 32) ? ~0ull : ((1ull << (2 * n)) - 1);
+  return n - __popcll(nz & mask);
+}
+
+// a / b correctly rounded, from y = RN(1/b): q = RN(a y) is within one ulp of
+// a/b, the residual a - b q is exact under FMA, and one more FMA gives the
+// correctly rounded quotient (Markstein; Muller et al., Handbook of
+// Floating-Point Arithmetic, the FMA-based division correction theorem).
+__device__ __forceinline__ double div_by_recip(double a, double b, double y) {
+  const double q = a * y;
+  const double r = fma(-q, b, a);
+  return fma(r, y, q);
+}
+
+struct GenParams {
+  const void *in;
+  void *out;
+  int64_t C;       // columns already produced (4^(n-r))
+  int64_t n_oh;    // 2^(r-J)
+  int64_t items;   // 3^(r-J) * 2^(r-J) * C
+  int r;           // qubits left before this pass
+  int n;
+  const double *wgt;     // 1/N_b per basis (weighted first pass)
+  double shots;          // N (final uniform)
+  int64_t total;         // N * 3^n (final uniform check)
+  int *status;
+  int64_t *T;            // optional: exact integers S_i 3^(n-k) for the integer assembly
+  double denom[16];      // N 3^k (uniform) or 3^k (weighted), exact
+  double recip[16];      // correctly rounded 1 / denom[k]
+  int64_t up3[16];       // 3^(n-k)
+};
+
+// One output column (ah, oh, c) of a fold pass.
+template <int J, typename InT, typename AccT, int MODE, bool WEIGHT>
+__device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
+  constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
+  constexpr int NO = 1 << J;
+  constexpr int NP = 1 << (2 * J);
+  const InT *__restrict__ in = static_cast<const InT *>(P.in);
+  const int64_t row_stride = (1ll << P.r) * P.C;  // al stride
+  const int64_t c = item % P.C;
+  const int64_t ahoh = item / P.C;
+  const int64_t oh = ahoh % P.n_oh;
+  const int64_t ah = ahoh / P.n_oh;
+  const int64_t base = ((ah * NA) << P.r) * P.C + (oh * NO) * P.C + c;
+  AccT acc[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) acc[p] = 0;
+#pragma unroll
+  for (int al = 0; al < NA; ++al) {
+    if constexpr (WEIGHT) {
+      int32_t v[NO];
+#pragma unroll
+      for (int ol = 0; ol < NO; ++ol) v[ol] = (int32_t)__ldg(in + base + al * row_stride + ol * P.C);
+      wht<J>(v);
+      const double w = __ldg(P.wgt + ah * NA + al);
+#pragma unroll
+      for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += (double)v[m] * w;
+    } else {
+      AccT v[NO];
+#pragma unroll
+      for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)__ldg(in + base + al * row_stride + ol * P.C);
+      wht<J>(v);
+#pragma unroll
+      for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
+    }
+  }
+  const int64_t obase = ahoh * NP * P.C + c;
+  if constexpr (MODE == M_STORE) {
+    AccT *out = static_cast<AccT *>(P.out);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = acc[p];
+  } else if constexpr (MODE == M_PARITY) {
+    int64_t *out = static_cast<int64_t *>(P.out);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = (int64_t)acc[p];
+  } else {
+    double *out = static_cast<double *>(P.out);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int64_t i = obase + p * P.C;  // ahoh == 0 in the last pass
+      const int k = identity_letters((uint64_t)i, P.n);
+      if constexpr (MODE == M_FINAL_U) {
+        if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
+        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
+        if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
+      } else {
+        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
+      }
+    }
+  }
+}
+
+// ---- step (ii) ----------------------------------------------------------------
+struct NumF64 {
+  using V = double2;
+  using In = double;
+};
+struct NumI64 {
+  using V = longlong2;
+  using In = long long;
+};
+
+struct LastScale {
+  float sh, sl;  // 1/(2^n N 3^n) = sh + sl (integer path only)
+};
+
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ longlong2 mk(long long a, long long b) { return make_longlong2(a, b); }
+
+// One qubit of the butterfly on (I, X, Y, Z) -> (00, 01, 10, 11).
+//   -i*Y = (Y.y, -Y.x);  +i*Y = (-Y.y, Y.x)
+__device__ __forceinline__ void m_qubit(double2 vI, double2 vX, double2 vY, double2 vZ, double2 &o00,
+                                        double2 &o01, double2 &o10, double2 &o11) {
+  o00 = mk(0.5 * (vI.x + vZ.x), 0.5 * (vI.y + vZ.y));
+  o11 = mk(0.5 * (vI.x - vZ.x), 0.5 * (vI.y - vZ.y));
+  o01 = mk(0.5 * (vX.x + vY.y), 0.5 * (vX.y - vY.x));
+  o10 = mk(0.5 * (vX.x - vY.y), 0.5 * (vX.y + vY.x));
+}
+__device__ __forceinline__ void m_qubit(longlong2 vI, longlong2 vX, longlong2 vY, longlong2 vZ,
+                                        longlong2 &o00, longlong2 &o01, longlong2 &o10, longlong2 &o11) {
+  o00 = mk(vI.x + vZ.x, vI.y + vZ.y);
+  o11 = mk(vI.x - vZ.x, vI.y - vZ.y);
+  o01 = mk(vX.x + vY.y, vX.y - vY.x);
+  o10 = mk(vX.x - vY.y, vX.y + vY.x);
+}
+
+__device__ __forceinline__ double2 load_first(const double *in, int64_t i) { return mk(__ldg(in + i), 0.0); }
+__device__ __forceinline__ longlong2 load_first(const long long *in, int64_t i) {
+  return mk(__ldg(in + i), 0ll);
+}
+
+// int64 -> float of v * (sh + sl), error about half an ulp of the float
+__device__ __forceinline__ float scaled(long long v, const LastScale &s) {
+  const float vh = (float)v;
+  const float vl = (float)(v - (long long)vh);
+  return __fmaf_rn(vh, s.sh, __fmaf_rn(vh, s.sl, vl * s.sh));
+}
+__device__ __forceinline__ float2 to_c64(double2 v, const LastScale &) {
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ float2 to_c64(longlong2 v, const LastScale &s) {
+  return make_float2(scaled(v.x, s), scaled(v.y, s));
+}
+
+struct AsmParams {
+  const void *in;
+  void *out;
+  int t;          // qubits already transformed
+  int n;
+  int64_t items;  // 4^(n-t-J) * 4^t
+  LastScale scale;
+};
+
+// One (P', R_lo, C_lo) item of an assembly pass over J <= 2 qubits.
+template <class Num, int J, bool FIRST, bool LAST>
+__device__ __forceinline__ void asm_item(const AsmParams &P, int64_t item) {
+  using V = typename Num::V;
+  constexpr int NP = 1 << (2 * J);
+  const int t = P.t;
+  const int tp = t + J;
+  const int64_t L4 = 1ll << (2 * t);  // 4^t
+  const int64_t L = item & (L4 - 1);
+  const int64_t Pp = item >> (2 * t);
+  const int64_t R_lo = L >> t, C_lo = L & ((1ll << t) - 1);
+  V v[NP];
+  const int64_t ibase = Pp * NP * L4 + L;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    if constexpr (FIRST)
+      v[p] = load_first(static_cast<const typename Num::In *>(P.in), ibase + p * L4);
+    else
+      v[p] = static_cast<const V *>(P.in)[ibase + p * L4];
+  }
+  // digit 0 (qubit t): index p = p1*4 + p0 -> u0 = 2 r0 + c0
+#pragma unroll
+  for (int h = 0; h < NP / 4; ++h) {
+    V a, b, c, d;
+    m_qubit(v[4 * h + 0], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3], a, b, c, d);
+    v[4 * h + 0] = a; v[4 * h + 1] = b; v[4 * h + 2] = c; v[4 * h + 3] = d;
+  }
+  if constexpr (J == 2) {
+#pragma unroll
+    for (int u0 = 0; u0 < 4; ++u0) {
+      V a, b, c, d;
+      m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
+      v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
+    }
+  }
+  // v[u1*4 + u0] with u_q = 2 r_q + c_q  ->  rj, cj
+  const int64_t W = 1ll << tp;
+  const int64_t obase = Pp * W * W;
+#pragma unroll
+  for (int u = 0; u < NP; ++u) {
+    int rj, cj;
+    if constexpr (J == 1) {
+      rj = u >> 1;
+      cj = u & 1;
+    } else {
+      const int u0 = u & 3, u1 = u >> 2;
+      rj = ((u1 >> 1) << 1) | (u0 >> 1);
+      cj = ((u1 & 1) << 1) | (u0 & 1);
+    }
+    const int64_t R = ((int64_t)rj << t) | R_lo;
+    const int64_t Cc = ((int64_t)cj << t) | C_lo;
+    const int64_t o = obase + R * W + Cc;
+    if constexpr (LAST)
+      static_cast<float2 *>(P.out)[o] = to_c64(v[u], P.scale);
+    else
+      static_cast<V *>(P.out)[o] = v[u];
+  }
+}
+
+}  // namespace passes
+}  // namespace lre

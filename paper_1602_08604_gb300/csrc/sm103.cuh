@@ -11,6 +11,13 @@ namespace lre {
 namespace sm103 {
 
 constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -48,14 +55,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Wait for completion of the phase with the given parity.  Returns false if
 // the wait gave up (spin limit) or another warp raised `abort`.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u) {
-      if (*abort) return false;
+      if (*abort || globaltimer() - t0 > kWaitNs) return false;
       __nanosleep(32);
     }
   }
-  return false;
 }
 
 // 2D TMA tile load global -> shared, completion counted on `bar` (bytes).

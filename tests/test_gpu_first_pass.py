@@ -40,3 +40,30 @@ def test_pipeline_equals_register_kernel(n, dt):
                         f"sample ref {outs[0][bad[:4]]} got {outs[1][bad[:4]]}")
     finally:
         lre.lre_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,dt", [(10, np.int16), (11, np.int32), (12, np.int16)])
+def test_fused_second_pass_equals_unfused(n, dt):
+    """The first pass fused with the second through L2 gives the same exact
+    integer parity sums as the two passes run separately."""
+    torch = need_gpu()
+    lre, ctx = ctx_and_lre()
+    L = lre.load()
+    f = L.lre_debug_set_first_pass
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_int
+    try:
+        from synth import gen
+        c = torch.empty((3 ** n, 2 ** n), dtype=torch.int16 if dt == np.int16 else torch.int32, device="cuda")
+        gen.gen_ghz(n, 0.05, 1000, 77 + n, c)
+        res = []
+        for variant in (1, 2):
+            assert f(ctx, variant) == 0
+            S = torch.empty(4 ** n, dtype=torch.int64, device="cuda")
+            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=1000)
+            lre.lre_sync(ctx)
+            res.append(S)
+        assert torch.equal(res[0], res[1])
+        assert int(res[1][0]) == 1000 * 3 ** n
+    finally:
+        lre.lre_destroy(ctx)
