@@ -74,6 +74,16 @@ typedef struct {
 } lre_c64;
 
 typedef struct CUstream_st *lre_stream; /* the same handle as cudaStream_t   */
+
+/* One instance of a batched run (lre_batch_run). */
+typedef struct {
+  const void *counts; /* device [3^n][2^n] counts of `kind`                     */
+  int32_t kind;       /* lre_count_kind                                          */
+  int32_t n;          /* qubits, 1 <= n <= 9                                     */
+  int64_t shots;      /* shots per basis (> 0), the same for every basis         */
+  double *theta;      /* device FP64 [4^n] output                                */
+  lre_c64 *rho;       /* device complex64 [2^n][2^n] output, or NULL             */
+} lre_instance;
 typedef struct lre_ctx lre_ctx;
 
 /* Create a context on CUDA device `device` (creates its cuSOLVER/cuBLAS
@@ -169,6 +179,25 @@ lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_base
 lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind host_kind,
                              int64_t shots_uniform, int n, double *theta_host, lre_c64 *rho_host,
                              lre_stream stream);
+
+/* Steps (i)+(ii) for many independent instances in ONE persistent kernel
+ * launch (the paper treats one state at a time; batching is for many small
+ * reconstructions).  Each instance gets exactly the result of lre_estimate
+ * with uniform shots (bit-identical theta; rho from the same exact-integer
+ * assembly).  descs: host array of `count` instance descriptors (copied
+ * during the call; the buffers they point to are device memory).  The pass
+ * lists of all instances are cut into 256-item work units that the CTAs of
+ * one grid claim in pass-major order; a unit waits (bounded by time, then
+ * LRE_ERR_TIMEOUT is latched) for its instance's previous pass.  n > 9 in
+ * any instance returns LRE_ERR_UNSUPPORTED (use lre_estimate). */
+lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream);
+
+/* Autotuner for lre_batch_run: times the candidate schedules (qubits per
+ * fold pass 2 or 3; 1, 2 or 4 resident CTAs per SM) on this batch, keeps the
+ * fastest in the context for later lre_batch_run calls, and returns its time
+ * per launch in *best_ms (may be NULL).  Synchronises `stream`. */
+lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream,
+                          float *best_ms);
 
 /* Synchronise `stream` and return (and clear) the first error latched by a
  * kernel since the last lre_sync. */

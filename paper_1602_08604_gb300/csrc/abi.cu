@@ -338,3 +338,18 @@ extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   ctx->first_variant = variant;
   return LRE_OK;
 }
+
+extern "C" lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream) {
+  if (!ctx) return LRE_ERR_INVALID_ARG;
+  lre_status st = set_device(ctx);
+  if (st != LRE_OK) return st;
+  return lre::batch_run(ctx, descs, count, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream,
+                                     float *best_ms) {
+  if (!ctx) return LRE_ERR_INVALID_ARG;
+  lre_status st = set_device(ctx);
+  if (st != LRE_OK) return st;
+  return lre::batch_tune(ctx, descs, count, reinterpret_cast<cudaStream_t>(stream), best_ms);
+}

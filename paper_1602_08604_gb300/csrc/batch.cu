@@ -1,0 +1,368 @@
+// Batched LRE: many small tomography instances (each n <= 9, its own shot
+// count) in ONE persistent kernel launch.
+//
+// Every instance has the pass list of lre_estimate with uniform shots: the
+// fold passes of step (i) (Sec. III, Eq. 3; at most JMAX qubits per pass in
+// registers, int32 partial sums, the last pass dividing by N 3^k and handing
+// the exact integers T = S 3^(n-k) on) and the exact-integer assembly passes
+// of step (ii) (Eq. 4).  All passes of all instances form one list ordered
+// pass-major (the first pass of every instance, then the second, ...), cut
+// into work units of 256 items.  Each CTA of the persistent grid claims
+// units from a device counter; a unit first waits (bounded by time) until
+// every unit of its instance's previous pass has finished, then runs.  The
+// pass-major order means a CTA only ever waits on units claimed before its
+// own, so with every CTA resident the launch always completes.
+//
+// The "schedule" (JMAX, CTAs per SM) is picked by lre_batch_tune, which times
+// the candidates on the caller's batch and keeps the fastest in the context.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lre_internal.cuh"
+#include "passes.cuh"
+#include "sm103.cuh"
+
+namespace lre {
+namespace {
+
+using namespace passes;
+
+// pass bodies a unit can run
+enum : int {
+  C_FOLD = 0,    // + (J-1)*4 + (in_i16 ? 0 : 2) + (final ? 1 : 0): J in 1..3 -> 0..11
+  C_ASM = 16,    // + (J-1)*4 + first*2 + last: J in 1..2 -> 16..23
+};
+
+struct BPhase {
+  int code;
+  int dep;          // index of the phase this one waits for (-1: none)
+  unsigned dep_units;
+  int pad;
+  int64_t unit_begin, units, items;
+  GenParams g;
+  AsmParams a;
+};
+
+struct BatchState {
+  unsigned long long next_unit;
+  int abort;
+};
+
+template <int JMAX>
+__device__ __forceinline__ void run_item(const BPhase &P, int64_t item) {
+  switch (P.code) {
+    case C_FOLD + 0: fold_item<1, int16_t, int32_t, M_STORE, false, true>(P.g, item); break;
+    case C_FOLD + 1: fold_item<1, int16_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
+    case C_FOLD + 2: fold_item<1, int32_t, int32_t, M_STORE, false, true>(P.g, item); break;
+    case C_FOLD + 3: fold_item<1, int32_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
+    case C_FOLD + 4: fold_item<2, int16_t, int32_t, M_STORE, false, true>(P.g, item); break;
+    case C_FOLD + 5: fold_item<2, int16_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
+    case C_FOLD + 6: fold_item<2, int32_t, int32_t, M_STORE, false, true>(P.g, item); break;
+    case C_FOLD + 7: fold_item<2, int32_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
+    case C_FOLD + 8:
+      if constexpr (JMAX >= 3) fold_item<3, int16_t, int32_t, M_STORE, false, true>(P.g, item);
+      break;
+    case C_FOLD + 9:
+      if constexpr (JMAX >= 3) fold_item<3, int16_t, int64_t, M_FINAL_U, false, true>(P.g, item);
+      break;
+    case C_FOLD + 10:
+      if constexpr (JMAX >= 3) fold_item<3, int32_t, int32_t, M_STORE, false, true>(P.g, item);
+      break;
+    case C_FOLD + 11:
+      if constexpr (JMAX >= 3) fold_item<3, int32_t, int64_t, M_FINAL_U, false, true>(P.g, item);
+      break;
+    case C_ASM + 0: asm_item<NumI64, 1, false, false>(P.a, item); break;
+    case C_ASM + 1: asm_item<NumI64, 1, false, true>(P.a, item); break;
+    case C_ASM + 2: asm_item<NumI64, 1, true, false>(P.a, item); break;
+    case C_ASM + 3: asm_item<NumI64, 1, true, true>(P.a, item); break;
+    case C_ASM + 4: asm_item<NumI64, 2, false, false>(P.a, item); break;
+    case C_ASM + 5: asm_item<NumI64, 2, false, true>(P.a, item); break;
+    case C_ASM + 6: asm_item<NumI64, 2, true, false>(P.a, item); break;
+    case C_ASM + 7: asm_item<NumI64, 2, true, true>(P.a, item); break;
+    default: break;
+  }
+}
+
+template <int JMAX>
+__global__ void __launch_bounds__(256) batch_kernel(const BPhase *__restrict__ ph, int nph,
+                                                   unsigned *__restrict__ done, BatchState *st,
+                                                   int64_t total_units, int *status) {
+  __shared__ int64_t s_unit;
+  __shared__ int s_phase, s_ok;
+  volatile int *abort = &st->abort;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long u = atomicAdd(&st->next_unit, 1ull);
+      int p = -1, ok = 1;
+      if ((int64_t)u < total_units && !*abort) {
+        int lo = 0, hi = nph - 1;  // last phase with unit_begin <= u
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ph[mid].unit_begin <= (int64_t)u) lo = mid;
+          else hi = mid - 1;
+        }
+        p = lo;
+        const int dep = ph[p].dep;
+        if (dep >= 0) {
+          const uint64_t t0 = sm103::globaltimer();
+          for (uint32_t it = 0;; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(done + dep) : "memory");
+            if (v >= ph[p].dep_units) break;
+            if ((it & 63u) == 63u) {
+              if (*abort || sm103::globaltimer() - t0 > sm103::kWaitNs) {
+                ok = 0;
+                break;
+              }
+              __nanosleep(64);
+            }
+          }
+        }
+      }
+      s_unit = (int64_t)u;
+      s_phase = p;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const int p = s_phase;
+    if (p < 0) break;
+    if (!s_ok) {
+      if (threadIdx.x == 0) {
+        *abort = 1;
+        latch(status, LRE_ERR_TIMEOUT);
+      }
+      break;
+    }
+    const BPhase &P = ph[p];
+    const int64_t item = (s_unit - P.unit_begin) * 256 + threadIdx.x;
+    if (item < P.items) run_item<JMAX>(P, item);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(done + p, 1u);
+  }
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+  std::vector<BPhase> phases;
+  size_t ws_bytes = 0;
+  int64_t total_units = 0;
+};
+
+// Per-instance pass lists, workspace offsets relative to `base`, then the
+// pass-major global order.
+Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
+  std::vector<std::vector<BPhase>> per(count);
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    const lre_instance &I = inst[i];
+    const int n = I.n;
+    // fold passes
+    int r = n, t = 0;
+    int64_t C = 1;
+    bool in16 = I.kind == LRE_COUNTS_I16;
+    const void *in = I.counts;
+    size_t bufA = 0, bufB = 0;
+    struct P0 {
+      int J, r;
+      int64_t C;
+      bool in16, last;
+    };
+    std::vector<P0> fp;
+    while (r > 0) {
+      const int J = std::min(r, jmax);
+      fp.push_back({J, r, C, in16, J == r});
+      const size_t ob = fp.back().last ? 0 : (size_t)ipow(6, r - J) * (size_t)ipow(4, J) * C * 4;
+      if (fp.size() % 2) bufA = std::max(bufA, ob);
+      else bufB = std::max(bufB, ob);
+      t += J;
+      r -= J;
+      C *= ipow(4, J);
+      in16 = false;
+    }
+    char *A = base + off;
+    off += up256(bufA);
+    char *Bf = base + off;
+    off += up256(bufB);
+    int64_t *T = nullptr;
+    char *ab[2] = {nullptr, nullptr};
+    if (I.rho) {
+      T = reinterpret_cast<int64_t *>(base + off);
+      off += up256((size_t)8 << (2 * n));
+      ab[0] = base + off;
+      off += up256((size_t)16 << (2 * n));
+      ab[1] = base + off;
+      off += up256((size_t)16 << (2 * n));
+    }
+    for (size_t k = 0; k < fp.size(); ++k) {
+      BPhase b{};
+      const P0 &q = fp[k];
+      b.code = C_FOLD + (q.J - 1) * 4 + (q.in16 ? 0 : 2) + (q.last ? 1 : 0);
+      GenParams &g = b.g;
+      g.in = in;
+      g.out = q.last ? static_cast<void *>(I.theta) : static_cast<void *>(k % 2 == 0 ? A : Bf);
+      g.C = q.C;
+      g.n_oh = 1ll << (q.r - q.J);
+      g.items = ipow(3, q.r - q.J) * g.n_oh * q.C;
+      g.r = q.r;
+      g.n = n;
+      g.shots = (double)I.shots;
+      g.total = I.shots * ipow(3, n);
+      g.T = T;
+      for (int kk = 0; kk < 16; ++kk) {
+        const double p3 = (double)ipow(3, kk <= n ? kk : 0);
+        g.denom[kk] = (double)I.shots * p3;
+        g.recip[kk] = 1.0 / g.denom[kk];
+        g.up3[kk] = kk <= n ? ipow(3, n - kk) : 0;
+      }
+      b.items = g.items;
+      per[i].push_back(b);
+      in = g.out;
+    }
+    if (I.rho) {
+      const LastScaleArgs sc = int_assembly_scale(n, I.shots);
+      int tt = 0, kk = 0;
+      const void *ain = T;
+      while (tt < n) {
+        const int J = (n - tt) >= 2 ? 2 : 1;
+        const bool first = tt == 0, last = tt + J == n;
+        BPhase b{};
+        b.code = C_ASM + (J - 1) * 4 + (first ? 2 : 0) + (last ? 1 : 0);
+        AsmParams &a = b.a;
+        a.in = ain;
+        a.out = last ? static_cast<void *>(I.rho) : static_cast<void *>(ab[kk & 1]);
+        a.t = tt;
+        a.n = n;
+        a.items = (1ll << (2 * (n - tt - J))) << (2 * tt);
+        a.scale = LastScale{sc.sh, sc.sl};
+        b.items = a.items;
+        per[i].push_back(b);
+        ain = a.out;
+        tt += J;
+        ++kk;
+      }
+    }
+  }
+  Plan plan;
+  plan.ws_bytes = off;
+  size_t maxp = 0;
+  for (auto &v : per) maxp = std::max(maxp, v.size());
+  std::vector<int> last_index(count, -1);
+  int64_t u = 0;
+  for (size_t k = 0; k < maxp; ++k) {
+    for (int i = 0; i < count; ++i) {
+      if (k >= per[i].size()) continue;
+      BPhase b = per[i][k];
+      b.units = (b.items + 255) / 256;
+      b.unit_begin = u;
+      u += b.units;
+      b.dep = last_index[i];
+      b.dep_units = b.dep >= 0 ? (unsigned)plan.phases[b.dep].units : 0;
+      last_index[i] = (int)plan.phases.size();
+      plan.phases.push_back(b);
+    }
+  }
+  plan.total_units = u;
+  return plan;
+}
+
+lre_status validate(const lre_instance *inst, int count) {
+  if (!inst || count <= 0) return LRE_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const lre_instance &I = inst[i];
+    if (!I.counts || !I.theta || I.shots <= 0) return LRE_ERR_INVALID_ARG;
+    if (I.kind != LRE_COUNTS_I16 && I.kind != LRE_COUNTS_I32) return LRE_ERR_INVALID_ARG;
+    if (I.n < 1) return LRE_ERR_INVALID_ARG;
+    if (I.n > 9) return LRE_ERR_UNSUPPORTED;
+    if ((double)I.shots * (double)ipow(3, I.n) >= 2147483647.0) return LRE_ERR_UNSUPPORTED;  // int32 partials
+  }
+  return LRE_OK;
+}
+
+}  // namespace
+
+lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s) {
+  lre_status st = validate(inst, count);
+  if (st != LRE_OK) return st;
+  const int jmax = ctx->batch_jmax;
+  // layout: [BatchState][done counters][phase table][instance workspaces]
+  Plan probe = build_plan(inst, count, jmax, nullptr);
+  const size_t nph = probe.phases.size();
+  const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) + up256(nph * sizeof(BPhase));
+  if ((st = ensure_workspace(ctx, head + probe.ws_bytes)) != LRE_OK) return st;
+  char *w = static_cast<char *>(ctx->ws);
+  BatchState *bs = reinterpret_cast<BatchState *>(w);
+  unsigned *done = reinterpret_cast<unsigned *>(w + up256(sizeof(BatchState)));
+  BPhase *dph = reinterpret_cast<BPhase *>(w + up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)));
+  Plan plan = build_plan(inst, count, jmax, w + head);
+  for (auto &b : plan.phases) b.g.status = ctx->d_status;
+  ctx->batch_host.resize(nph * sizeof(BPhase));
+  std::copy(reinterpret_cast<const char *>(plan.phases.data()),
+            reinterpret_cast<const char *>(plan.phases.data()) + nph * sizeof(BPhase), ctx->batch_host.data());
+  cudaError_t e = cudaMemsetAsync(w, 0, up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dph, ctx->batch_host.data(), nph * sizeof(BPhase), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch plan upload");
+  int per_sm = 0;
+  if (jmax >= 3)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<3>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<2>, 256, 0);
+  per_sm = std::max(1, std::min(per_sm, ctx->batch_ctas_per_sm));
+  const int grid = ctx->num_sms * per_sm;  // every CTA resident: waits always resolve
+  {
+    Launch L(ctx, "batch_kernel", s);
+    if (jmax >= 3)
+      batch_kernel<3><<<grid, 256, 0, s>>>(dph, (int)nph, done, bs, plan.total_units, ctx->d_status);
+    else
+      batch_kernel<2><<<grid, 256, 0, s>>>(dph, (int)nph, done, bs, plan.total_units, ctx->d_status);
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "batch kernel launch");
+}
+
+lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s, float *best_ms) {
+  lre_status st = validate(inst, count);
+  if (st != LRE_OK) return st;
+  const int cand_j[2] = {2, 3};
+  const int cand_occ[3] = {1, 2, 4};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return LRE_ERR_CUDA;
+  }
+  float best = 1e30f;
+  int bj = ctx->batch_jmax, bo = ctx->batch_ctas_per_sm;
+  for (int j : cand_j) {
+    for (int o : cand_occ) {
+      ctx->batch_jmax = j;
+      ctx->batch_ctas_per_sm = o;
+      if ((st = batch_run(ctx, inst, count, s)) != LRE_OK) break;  // warm-up
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && st == LRE_OK; ++rep) st = batch_run(ctx, inst, count, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = LRE_ERR_CUDA;
+      if (st != LRE_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 3.f;
+      if (ms < best) {
+        best = ms;
+        bj = j;
+        bo = o;
+      }
+    }
+    if (st != LRE_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->batch_jmax = bj;
+  ctx->batch_ctas_per_sm = bo;
+  if (best_ms) *best_ms = best;
+  return st;
+}
+
+}  // namespace lre

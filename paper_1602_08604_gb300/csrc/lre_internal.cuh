@@ -35,6 +35,9 @@ struct lre_ctx {
   // pipeline fused with the second pass through L2 (correct, but slower on
   // GB300 so far: its second-pass jobs are L2-latency bound)
   int first_variant = 1;
+  int batch_jmax = 3;         // batched schedule: qubits per fold pass
+  int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
+  std::vector<char> batch_host;  // host copy of the last batched pass table
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
@@ -103,6 +106,10 @@ lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
 // ---- end to end from host memory ---------------------------------------------
 lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, int64_t shots,
                              int n, double *theta_host, lre_c64 *rho_host, cudaStream_t s);
+
+// ---- batched instances (one persistent launch) ---------------------------------
+lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);
+lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s, float *best_ms);
 
 // ---- ingest ------------------------------------------------------------------
 lre_status histogram_run(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,

@@ -84,8 +84,16 @@ struct GenParams {
   int64_t up3[16];       // 3^(n-k)
 };
 
+// Loads of pass inputs: the read-only path, or (COHERENT) straight from L2 for
+// inputs written earlier by the same kernel launch (the batched kernel).
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld_in(const T *p) {
+  if constexpr (COHERENT) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // One output column (ah, oh, c) of a fold pass.
-template <int J, typename InT, typename AccT, int MODE, bool WEIGHT>
+template <int J, typename InT, typename AccT, int MODE, bool WEIGHT, bool COHERENT = false>
 __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
   constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
   constexpr int NO = 1 << J;
@@ -105,7 +113,7 @@ __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
     if constexpr (WEIGHT) {
       int32_t v[NO];
 #pragma unroll
-      for (int ol = 0; ol < NO; ++ol) v[ol] = (int32_t)__ldg(in + base + al * row_stride + ol * P.C);
+      for (int ol = 0; ol < NO; ++ol) v[ol] = (int32_t)ld_in<COHERENT>(in + base + al * row_stride + ol * P.C);
       wht<J>(v);
       const double w = __ldg(P.wgt + ah * NA + al);
 #pragma unroll
@@ -113,7 +121,7 @@ __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
     } else {
       AccT v[NO];
 #pragma unroll
-      for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)__ldg(in + base + al * row_stride + ol * P.C);
+      for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)ld_in<COHERENT>(in + base + al * row_stride + ol * P.C);
       wht<J>(v);
 #pragma unroll
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
@@ -179,9 +187,9 @@ __device__ __forceinline__ void m_qubit(longlong2 vI, longlong2 vX, longlong2 vY
   o10 = mk(vX.x - vY.y, vX.y + vY.x);
 }
 
-__device__ __forceinline__ double2 load_first(const double *in, int64_t i) { return mk(__ldg(in + i), 0.0); }
+__device__ __forceinline__ double2 load_first(const double *in, int64_t i) { return mk(__ldcg(in + i), 0.0); }
 __device__ __forceinline__ longlong2 load_first(const long long *in, int64_t i) {
-  return mk(__ldg(in + i), 0ll);
+  return mk(__ldcg(in + i), 0ll);
 }
 
 // int64 -> float of v * (sh + sl), error about half an ulp of the float
@@ -224,7 +232,7 @@ __device__ __forceinline__ void asm_item(const AsmParams &P, int64_t item) {
     if constexpr (FIRST)
       v[p] = load_first(static_cast<const typename Num::In *>(P.in), ibase + p * L4);
     else
-      v[p] = static_cast<const V *>(P.in)[ibase + p * L4];
+      v[p] = __ldcg(static_cast<const V *>(P.in) + ibase + p * L4);
   }
   // digit 0 (qubit t): index p = p1*4 + p0 -> u0 = 2 r0 + c0
 #pragma unroll

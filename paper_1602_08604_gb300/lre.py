@@ -27,6 +27,12 @@ LRE_HOST_COUNTS_I32 = 0
 LRE_HOST_COUNTS_I16 = 1
 LRE_HOST_RECORDS_U16 = 2
 
+class lre_instance(ctypes.Structure):
+    """Mirror of the C struct lre_instance (one batched instance)."""
+    _fields_ = [("counts", ctypes.c_void_p), ("kind", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("shots", ctypes.c_int64), ("theta", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
+
+
 # (name, restype, argtypes) for every symbol declared in include/lre.h
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -44,6 +50,8 @@ SIGNATURES = [
     ("lre_project", _i, [_p, _p, _i, _p, _p, _p, _p]),
     ("lre_histogram", _i, [_p, _p, _i64, _i64, _i, _p, _i, _p]),
     ("lre_estimate_host", _i, [_p, _p, _i, _i64, _i, _p, _p, _p]),
+    ("lre_batch_run", _i, [_p, _p, _i, _p]),
+    ("lre_batch_tune", _i, [_p, _p, _i, _p, ctypes.POINTER(ctypes.c_float)]),
     ("lre_sync", _i, [_p, _p]),
     ("lre_status_string", ctypes.c_char_p, [_i]),
     ("lre_last_error", ctypes.c_char_p, [_p]),
@@ -172,6 +180,28 @@ def lre_estimate_host(ctx, host_in, host_kind, shots, n, theta_host, rho_host=No
     """host_in / theta_host / rho_host: pinned CPU tensors (data pointers only)."""
     _check(load().lre_estimate_host(ctx, _ptr(host_in), int(host_kind), int(shots), int(n),
                                     _ptr(theta_host), _ptr(rho_host), _stream(stream)), ctx)
+
+
+def _instances(items):
+    """items: iterable of (counts, shots, n, theta, rho_or_None) device tensors."""
+    arr = (lre_instance * len(items))()
+    for k, (counts, shots, n, theta, rho) in enumerate(items):
+        arr[k] = lre_instance(_ptr(counts), _kind(counts), int(n), int(shots), _ptr(theta), _ptr(rho))
+    return arr
+
+
+def lre_batch_run(ctx, items, stream=None):
+    arr = items if isinstance(items, ctypes.Array) else _instances(items)
+    _check(load().lre_batch_run(ctx, ctypes.cast(arr, ctypes.c_void_p), len(arr), _stream(stream)), ctx)
+
+
+def lre_batch_tune(ctx, items, stream=None):
+    """Pick the fastest batched schedule for this batch; returns ms per launch."""
+    arr = items if isinstance(items, ctypes.Array) else _instances(items)
+    ms = ctypes.c_float()
+    _check(load().lre_batch_tune(ctx, ctypes.cast(arr, ctypes.c_void_p), len(arr), _stream(stream),
+                                 ctypes.byref(ms)), ctx)
+    return ms.value
 
 
 def lre_sync(ctx, stream=None):

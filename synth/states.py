@@ -76,11 +76,12 @@ def pauli_expectations(rho):
     r = np.arange(d)
     out = np.zeros(4 ** n, dtype=np.float64)
     xs = binary_digits(np.arange(d), n)            # (d, n) bits of x (and of z)
+    popc = xs.sum(axis=1)                          # popcount of 0..d-1
+    z = np.arange(d)
     for x in range(d):
         v = rho[r ^ x, r]                          # Tr picks rho[c, r] P[r, c]
         w = _fwht_last(v.real) + 1j * _fwht_last(v.imag)   # sum_r v[r](-1)^{r.z}
-        z = np.arange(d)
-        xz = np.array([bin(x & int(zz)).count("1") for zz in z])
+        xz = popc[x & z]
         ph = (-1j) ** xz
         val = (ph * w).real
         xd = xs[x]

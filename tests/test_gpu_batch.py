@@ -1,0 +1,88 @@
+"""Batched form: many instances of uneven n and shots in one persistent
+launch give exactly the per-instance lre_estimate results (and the oracle's
+theta bit for bit where the oracle is fast)."""
+import numpy as np
+import pytest
+
+from oracle import direct
+from synth import counts as sc
+from synth import states as st
+from tests.gpu_util import ctx_and_lre, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _instance(n, seed, shots, dtype):
+    rho = st.ginibre_mixture(n, 1 + seed % 4, seed=seed)
+    thr = sc.cdf_thresholds(st.born_probabilities(st.pauli_expectations(rho), n))
+    return sc.sample_cdf(thr, shots, seed=seed + 7, dtype=dtype)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    torch = need_gpu()
+    rng = np.random.default_rng(11)
+    specs = [(n, int(np.exp(rng.uniform(np.log(500), np.log(10000)))), dt)
+             for n, dt in [(1, np.int32), (2, np.int16), (3, np.int32), (4, np.int32), (5, np.int16),
+                           (6, np.int32), (7, np.int32), (7, np.int16), (8, np.int32), (9, np.int32),
+                           (3, np.int16), (5, np.int32)]]
+    items, host = [], []
+    for k, (n, shots, dt) in enumerate(specs):
+        c = _instance(n, 40 + k, shots, dt)
+        host.append((c, shots, n))
+        theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+        rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda") if k % 5 != 3 else None
+        items.append((torch.from_numpy(c).cuda(), shots, n, theta, rho))
+    return torch, items, host
+
+
+def _check_against_single(torch, lre, ctx, items, host):
+    for (c, shots, n, theta, rho), (ch, _, _) in zip(items, host):
+        t1 = torch.empty_like(theta)
+        r1 = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda") if rho is not None else None
+        lre.lre_estimate(ctx, c, shots, n, t1, r1)
+        lre.lre_sync(ctx)
+        assert torch.equal(theta, t1), n
+        if rho is not None:
+            assert torch.equal(rho, r1), n
+        if n <= 6:
+            np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(ch, shots, n))
+
+
+def test_batch_equals_per_instance_and_oracle(batch):
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    try:
+        lre.lre_batch_run(ctx, items)
+        lre.lre_sync(ctx)
+        _check_against_single(torch, lre, ctx, items, host)
+    finally:
+        lre.lre_destroy(ctx)
+
+
+def test_batch_tune_then_run(batch):
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    try:
+        ms = lre.lre_batch_tune(ctx, items)
+        assert ms > 0
+        for _, _, _, theta, rho in items:
+            theta.fill_(float("nan"))
+        lre.lre_batch_run(ctx, items)
+        lre.lre_sync(ctx)
+        _check_against_single(torch, lre, ctx, items, host)
+    finally:
+        lre.lre_destroy(ctx)
+
+
+def test_batch_rejects_large_n(batch):
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    try:
+        c = torch.zeros((3 ** 10, 2 ** 10), dtype=torch.int32, device="cuda")
+        th = torch.empty(4 ** 10, dtype=torch.float64, device="cuda")
+        with pytest.raises(lre.LreError) as e:
+            lre.lre_batch_run(ctx, [(c, 100, 10, th, None)])
+        assert e.value.status == lre.LRE_ERR_UNSUPPORTED
+    finally:
+        lre.lre_destroy(ctx)
