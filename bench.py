@@ -371,6 +371,89 @@ def run_ours(args, wl):
     return out
 
 
+def batched_specs(count=256, seed=256):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(3, 10))
+        rank = int(rng.integers(1, 5))
+        shots = int(np.exp(rng.uniform(np.log(500), np.log(10000))))
+        out.append((n, rank, shots, seed * 1000 + k))
+    return out
+
+
+def run_batched(args):
+    """256 instances (n ~ U{3..9}, random-rank Ginibre mixtures, shots
+    log-uniform in 500..10000, int32 counts) in one persistent launch, against
+    one lre_estimate call per instance."""
+    import numpy as np
+    import torch
+    from paper_1602_08604_gb300 import lre
+    from synth import counts as sc
+    from synth import gen
+    from synth import states as st
+    device = torch.device("cuda", 0)
+    specs = batched_specs()
+    items = []
+    for n, rank, shots, seed in specs:
+        rho = st.ginibre_mixture(n, rank, seed)
+        thr = sc.cdf_thresholds(st.born_probabilities(st.pauli_expectations(rho), n))
+        c = torch.empty((3 ** n, 2 ** n), dtype=torch.int32, device=device)
+        gen.gen_cdf(torch.from_numpy(thr.view(np.int32)).to(device), n, shots, seed, c)
+        theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
+        rh = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
+        items.append((c, shots, n, theta, rh))
+    torch.cuda.synchronize()
+    ctx = lre.lre_create(0)
+    stream = torch.cuda.current_stream(device)
+    tuned_ms = lre.lre_batch_tune(ctx, items, stream=stream)
+    bases = sum(3 ** n for n, _, _, _ in specs)
+    count_bytes = sum(3 ** n * 2 ** n * 4 for n, _, _, _ in specs)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    launches0 = lre.lre_launch_count(ctx)
+    ms_batch = timed(lambda: lre.lre_batch_run(ctx, items, stream=stream))
+    batch_launches = (lre.lre_launch_count(ctx) - launches0) // (args.steps + args.warmup)
+    theta_b = [it[3].clone() for it in items]
+    launches0 = lre.lre_launch_count(ctx)
+    ms_single = timed(lambda: [lre.lre_estimate(ctx, c, s, n, t, r, stream=stream) for c, s, n, t, r in items])
+    single_launches = (lre.lre_launch_count(ctx) - launches0) // (args.steps + args.warmup)
+    same = all(torch.equal(a, it[3]) for a, it in zip(theta_b, items))
+    lre.lre_sync(ctx, stream)
+    peak, peak_kind = load_peaks()
+    out = {
+        "metric": "Pauli bases/sec (batched instances)", "value": round(bases / (ms_batch / 1e3), 1),
+        "unit": "Pauli bases/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_batch, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+        "config": {"workload": "256 instances, n ~ U{3..9}, random-rank (1..4) Ginibre mixtures, "
+                               "shots/basis log-uniform 500..10000, int32 counts",
+                   "bases": bases, "count_bytes": count_bytes,
+                   "schedule": {"tuned_ms": round(tuned_ms, 4)}},
+        "batched": {"ms": round(ms_batch, 4), "launches_per_step": batch_launches,
+                    "count_gbs": round(count_bytes / (ms_batch / 1e3) / 1e9, 1),
+                    "frac_hbm_counts": round(count_bytes / (ms_batch / 1e3) / 1e9 / peak, 4)},
+        "one_launch_per_instance": {"ms": round(ms_single, 4), "launches_per_step": single_launches},
+        "speedup_vs_per_instance": round(ms_single / ms_batch, 2),
+        "theta_equal_batched_vs_single": same, "gpu_launches": batch_launches * args.steps,
+    }
+    lre.lre_destroy(ctx)
+    return out
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -400,7 +483,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="n14", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="n14", choices=sorted(WORKLOADS) + ["batched"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -408,6 +491,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     args = ap.parse_args()
+    if args.workload == "batched":
+        out = run_batched(args) if args.impl == "ours" else None
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
     wl = WORKLOADS[args.workload]
     out = run_reference(args, wl) if args.impl == "reference" else run_ours(args, wl)
     if out is not None:

@@ -199,6 +199,21 @@ lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre
 lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream,
                           float *best_ms);
 
+/* First fold pass of step (i) on later calls of this context:
+ * LRE_FOLD_FWHT (default): the parity transform (Walsh-Hadamard butterflies)
+ *   and the ternary fold on the integer ALUs;
+ * LRE_FOLD_TENSOR: the same contraction of the first three qubits as a GEMM
+ *   on the 5th-generation tensor cores (tcgen05.mma kind::f16 with FP32
+ *   accumulation in TMEM) against the constant +-1/0 matrix of Sec. III's
+ *   per-qubit Gamma structure, exact because every count is an fp16 integer
+ *   and every partial sum stays below 2^24 (bit-identical to FWHT).  It
+ *   applies to int16 counts with shots per basis (hence every count) below
+ *   1024; other calls run the FWHT path.  The first switch to TENSOR
+ *   allocates a 56 KiB operand buffer in the context. */
+#define LRE_FOLD_FWHT 0
+#define LRE_FOLD_TENSOR 1
+lre_status lre_set_fold_path(lre_ctx *ctx, int path);
+
 /* Synchronise `stream` and return (and clear) the first error latched by a
  * kernel since the last lre_sync. */
 lre_status lre_sync(lre_ctx *ctx, lre_stream stream);

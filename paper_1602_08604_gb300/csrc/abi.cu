@@ -161,6 +161,7 @@ void lre_destroy(lre_ctx *ctx) {
   if (ctx->blas) cublasDestroy(reinterpret_cast<cublasHandle_t>(ctx->blas));
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->mma_operand) cudaFree(ctx->mma_operand);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (int k = 0; k < 2; ++k) {
     if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);
@@ -352,4 +353,23 @@ extern "C" lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, in
   lre_status st = set_device(ctx);
   if (st != LRE_OK) return st;
   return lre::batch_tune(ctx, descs, count, reinterpret_cast<cudaStream_t>(stream), best_ms);
+}
+
+extern "C" lre_status lre_set_fold_path(lre_ctx *ctx, int path) {
+  if (!ctx || (path != LRE_FOLD_FWHT && path != LRE_FOLD_TENSOR)) return LRE_ERR_INVALID_ARG;
+  lre_status st = set_device(ctx);
+  if (st != LRE_OK) return st;
+  if (path == LRE_FOLD_TENSOR && !ctx->mma_operand) {
+    cudaError_t e = cudaMalloc(&ctx->mma_operand, lre::mma_operand_bytes());
+    if (e != cudaSuccess) {
+      ctx->mma_operand = nullptr;
+      cudaGetLastError();
+      return lre::cuda_fail(ctx, e, "tensor-core operand");
+    }
+    if ((st = lre::mma_operand_upload(ctx, ctx->mma_operand, nullptr)) != LRE_OK) return st;
+    e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return lre::cuda_fail(ctx, e, "tensor-core operand");
+  }
+  ctx->fold_path = path;
+  return LRE_OK;
 }

@@ -675,7 +675,12 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
     else
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
     CUtensorMap tmap;
-    if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
+    const bool tensor = pp.first6 && !pp.fused9 && ctx->fold_path == 1 && ctx->mma_operand &&
+                        pp.in_t == T_I16 && a.shots_uniform > 0 && a.shots_uniform < 1024;
+    if (tensor && make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r))) {
+      lre_status st = mma_first_pass(ctx, tmap, ctx->mma_operand, static_cast<int32_t *>(out), pp.r, s);
+      if (st != LRE_OK) return st;
+    } else if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
         make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {
       const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
       int grid = ctx->num_sms;

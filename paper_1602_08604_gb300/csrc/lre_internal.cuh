@@ -1,5 +1,6 @@
 // Internal declarations shared by the translation units of liblre.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -35,6 +36,8 @@ struct lre_ctx {
   // pipeline fused with the second pass through L2 (correct, but slower on
   // GB300 so far: its second-pass jobs are L2-latency bound)
   int first_variant = 1;
+  int fold_path = 0;          // 0 FWHT on the ALU, 1 tensor cores for the first pass
+  void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
   std::vector<char> batch_host;  // host copy of the last batched pass table
@@ -106,6 +109,12 @@ lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
 // ---- end to end from host memory ---------------------------------------------
 lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, int64_t shots,
                              int n, double *theta_host, lre_c64 *rho_host, cudaStream_t s);
+
+// ---- tensor-core first pass (fold_mma.cu) ----------------------------------------
+size_t mma_operand_bytes();
+lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
+lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &tmap, const void *a_dev, int32_t *out, int n,
+                          cudaStream_t s);
 
 // ---- batched instances (one persistent launch) ---------------------------------
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);

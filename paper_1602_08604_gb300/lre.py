@@ -23,6 +23,9 @@ LRE_ERR_EIG_FAILED = 7
 LRE_COUNTS_I32 = 0
 LRE_COUNTS_I16 = 1
 
+LRE_FOLD_FWHT = 0
+LRE_FOLD_TENSOR = 1
+
 LRE_HOST_COUNTS_I32 = 0
 LRE_HOST_COUNTS_I16 = 1
 LRE_HOST_RECORDS_U16 = 2
@@ -52,6 +55,7 @@ SIGNATURES = [
     ("lre_estimate_host", _i, [_p, _p, _i, _i64, _i, _p, _p, _p]),
     ("lre_batch_run", _i, [_p, _p, _i, _p]),
     ("lre_batch_tune", _i, [_p, _p, _i, _p, ctypes.POINTER(ctypes.c_float)]),
+    ("lre_set_fold_path", _i, [_p, _i]),
     ("lre_sync", _i, [_p, _p]),
     ("lre_status_string", ctypes.c_char_p, [_i]),
     ("lre_last_error", ctypes.c_char_p, [_p]),
@@ -202,6 +206,11 @@ def lre_batch_tune(ctx, items, stream=None):
     _check(load().lre_batch_tune(ctx, ctypes.cast(arr, ctypes.c_void_p), len(arr), _stream(stream),
                                  ctypes.byref(ms)), ctx)
     return ms.value
+
+
+def lre_set_fold_path(ctx, path):
+    """LRE_FOLD_FWHT (default) or LRE_FOLD_TENSOR (tcgen05 first pass)."""
+    _check(load().lre_set_fold_path(ctx, int(path)), ctx)
 
 
 def lre_sync(ctx, stream=None):
