@@ -270,6 +270,8 @@ def run_ours(args, wl):
     theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
     rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
     ctx = lre.lre_create(local)
+    if args.fold_path == "tensor":
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -318,6 +320,8 @@ def run_ours(args, wl):
     count_bytes = (2 if wl["kind"] == "i16" else 4)
     alg_bytes = {  # algorithmic bytes per launch of each kernel
         "fold_first6": B * (2 ** n) * count_bytes,
+        "fold_first6_mma": B * (2 ** n) * count_bytes,
+        "fold_first9_fused": B * (2 ** n) * count_bytes,
     }.get(top_name)
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if alg_bytes else None
@@ -357,6 +361,7 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "shots_per_basis": wl["shots"],
                        "counts_dtype": wl["kind"], "step": "lre_estimate: counts -> theta (FP64) -> rho (c64)",
+                       "fold_path": args.fold_path,
                        "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
@@ -488,6 +493,8 @@ def main():
     ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fold-path", default="fwht", choices=["fwht", "tensor"],
+                    help="first fold pass on the ALUs (FWHT) or on the tensor cores")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     args = ap.parse_args()

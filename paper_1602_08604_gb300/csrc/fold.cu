@@ -125,11 +125,12 @@ __global__ void __launch_bounds__(P1_THREADS, 2)
 //   warp 0      producer: one 2D TMA load per sub-tile (81 rows x 64
 //               outcomes = the two top ternary digits of the tile fixed) into
 //               a ring of R shared-memory slots, completion on mbarriers.
-//   warps 1..6  level A: one sub-tile per warp, lane = (a3, olB) for 24
+//   warps 1..5  level A: one sub-tile per warp, lane = (a3, olB) for 24
 //               lanes, 27 rows x 8 outcomes from shared memory -> 64 partial
 //               sums -> exchange buffer Z[tile parity].
-//   warps 7..8  level B: one thread per level-A Pauli triple, 27 x 8
+//   warps 6..7  level B: one thread per level-A Pauli triple, 27 x 8
 //               partials -> 64 outputs -> HBM.
+//   warps 8..9  (fused variant only) the second pass, see FUSE_* below.
 // Loads never sit in registers, so up to R sub-tiles (R x 10.4 KB for int16)
 // are in flight per SM while the ALU warps work.  Every wait is bounded; a
 // timed-out wait latches LRE_ERR_TIMEOUT and the CTA drains and exits.
@@ -226,8 +227,8 @@ __device__ __forceinline__ void lds_row8<int32_t>(const int32_t *p, int32_t (&v)
   v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
-template <typename InT>
-__global__ void __launch_bounds__(FUSE_THREADS, 1)
+template <typename InT, bool FUSE>
+__global__ void __launch_bounds__(FUSE ? FUSE_THREADS : PIPE_THREADS, 1)
     fold_first6_pipe(const __grid_constant__ CUtensorMap tmap, PipeArgs A) {
   int32_t *__restrict__ out = A.out;
   const int n = A.n;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(FUSE_THREADS, 1)
       int64_t g = 0;
       for (int64_t tile = tile_begin + blockIdx.x; tile < tile_end && !*abort_flag; tile += gridDim.x) {
         int64_t ah, oh;
-        tile_coords(A.fuse, tile, n_oh, ah, oh);
+        tile_coords(FUSE ? 1 : 0, tile, n_oh, ah, oh);
         for (int s = 0; s < 9; ++s, ++g) {
           const int w = (int)(g % PIPE_A_WARPS);
           const int64_t j = g / PIPE_A_WARPS;
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(FUSE_THREADS, 1)
       }
       int32_t *dst = out + tile * 4096;
       int slot = 0;
-      if (A.fuse) {
+      if constexpr (FUSE) {
         // ring slot of this tile's group; wait until the slot's previous group
         // has been read by all of its second-pass jobs
         const int64_t G = tile / 216;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(FUSE_THREADS, 1)
       }
       sm103::mbar_arrive(&zempty[zb]);
       int32_t *o = dst + tb;
-      if (A.fuse) {
+      if constexpr (FUSE) {
 #pragma unroll
         for (int p = 0; p < 64; ++p) o[p * 64] = acc[p];  // stays in L2 for the second pass
         __threadfence();
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(FUSE_THREADS, 1)
         for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
       }
     }
-  } else if (A.fuse) {
+  } else if (FUSE) {
     // second pass (qubits 6..8) over finished groups, one 32-column job per
     // warp: input the group's 216 tile outputs (27 a-digit x 8 o-bit
     // combinations) from L2, output [G][64][4096] like fold_generic<3>.
@@ -703,12 +704,14 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       Launch L(ctx, pp.fused9 ? "fold_first9_fused" : "fold_first6", s);
       if (pp.in_t == T_I16) {
         constexpr int sm = PipeCfg<int16_t>::SMEM;
-        cudaFuncSetAttribute(fold_first6_pipe<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        fold_first6_pipe<int16_t><<<grid, threads, sm, s>>>(tmap, A);
+        auto k = pp.fused9 ? fold_first6_pipe<int16_t, true> : fold_first6_pipe<int16_t, false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        k<<<grid, threads, sm, s>>>(tmap, A);
       } else {
         constexpr int sm = PipeCfg<int32_t>::SMEM;
-        cudaFuncSetAttribute(fold_first6_pipe<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        fold_first6_pipe<int32_t><<<grid, threads, sm, s>>>(tmap, A);
+        auto k = pp.fused9 ? fold_first6_pipe<int32_t, true> : fold_first6_pipe<int32_t, false>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        k<<<grid, threads, sm, s>>>(tmap, A);
       }
     } else if (pp.first6 && !pp.fused9) {
       const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
@@ -782,12 +785,12 @@ extern "C" lre_status lre_debug_first_pass(lre_ctx *ctx, const void *counts, lre
     A.status = ctx->d_status;
     if (kind == LRE_COUNTS_I16) {
       constexpr int sm = PipeCfg<int16_t>::SMEM;
-      cudaFuncSetAttribute(fold_first6_pipe<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      fold_first6_pipe<int16_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, A);
+      cudaFuncSetAttribute(fold_first6_pipe<int16_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      fold_first6_pipe<int16_t, false><<<grid, PIPE_THREADS, sm, s>>>(tmap, A);
     } else {
       constexpr int sm = PipeCfg<int32_t>::SMEM;
-      cudaFuncSetAttribute(fold_first6_pipe<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-      fold_first6_pipe<int32_t><<<grid, PIPE_THREADS, sm, s>>>(tmap, A);
+      cudaFuncSetAttribute(fold_first6_pipe<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+      fold_first6_pipe<int32_t, false><<<grid, PIPE_THREADS, sm, s>>>(tmap, A);
     }
   } else {
     const size_t smem = 64 * P1_ZSTRIDE * sizeof(int32_t);
