@@ -335,6 +335,26 @@ def run_ours(args, wl):
     step_alg = B * (2 ** n) * count_bytes + 8 * 4 ** n * 2 + 8 * 4 ** n
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in per.items()}
     check = spot_check(torch, wl, theta, rho) if args.check and rank == 0 else None
+    projection = None
+    if args.project and rank == 0:
+        # step (iii), timed on its own: FP64 eigendecomposition (cuSOLVER),
+        # simplex correction and rank-k rebuild of the rho of the last step
+        rho_p = torch.empty_like(rho)
+        eig = torch.empty(2 ** n, dtype=torch.float64, device=device)
+        lre.lre_project(ctx, rho, n, rho_p, eig_rho=eig, stream=stream)  # warm-up (handles, workspace)
+        torch.cuda.synchronize()
+        lre.lre_profile(ctx, True)
+        t0 = time.perf_counter()
+        lre.lre_project(ctx, rho, n, rho_p, eig_rho=eig, stream=stream)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        precs = lre.lre_profile_records(ctx)
+        lre.lre_profile(ctx, False)
+        ev = eig.cpu().numpy()
+        projection = {"seconds": round(secs, 4), "kernels_ms": {k: round(v, 3) for k, v in precs},
+                      "kept_eigenvalues": int((ev > 0).sum()), "trace": float(ev.sum()),
+                      "min_eigenvalue": float(ev.min())}
+        del rho_p
     lre.lre_destroy(ctx)
     ctx = None
     e2e = None
@@ -373,6 +393,8 @@ def run_ours(args, wl):
         if check:
             out["parity"] = check
         out["e2e"] = e2e
+        if projection:
+            out["projection"] = projection
     return out
 
 
@@ -493,6 +515,7 @@ def main():
     ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--project", action="store_true", help="also time step (iii) once")
     ap.add_argument("--fold-path", default="fwht", choices=["fwht", "tensor"],
                     help="first fold pass on the ALUs (FWHT) or on the tensor cores")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

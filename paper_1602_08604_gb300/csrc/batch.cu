@@ -31,8 +31,8 @@ using namespace passes;
 
 // pass bodies a unit can run
 enum : int {
-  C_FOLD = 0,    // + (J-1)*4 + (in_i16 ? 0 : 2) + (final ? 1 : 0): J in 1..3 -> 0..11
-  C_ASM = 16,    // + (J-1)*4 + first*2 + last: J in 1..2 -> 16..23
+  C_FOLD = 0,    // + (J-1)*8 + first*4 + (in_i16 ? 0 : 2) + (final ? 1 : 0): J in 1..3 -> 0..23
+  C_ASM = 32,    // + (J-1)*4 + first*2 + last: J in 1..2 -> 32..39
 };
 
 struct BPhase {
@@ -53,25 +53,45 @@ struct BatchState {
 template <int JMAX>
 __device__ __forceinline__ void run_item(const BPhase &P, int64_t item) {
   switch (P.code) {
-    case C_FOLD + 0: fold_item<1, int16_t, int32_t, M_STORE, false, true>(P.g, item); break;
-    case C_FOLD + 1: fold_item<1, int16_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
-    case C_FOLD + 2: fold_item<1, int32_t, int32_t, M_STORE, false, true>(P.g, item); break;
-    case C_FOLD + 3: fold_item<1, int32_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
-    case C_FOLD + 4: fold_item<2, int16_t, int32_t, M_STORE, false, true>(P.g, item); break;
-    case C_FOLD + 5: fold_item<2, int16_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
-    case C_FOLD + 6: fold_item<2, int32_t, int32_t, M_STORE, false, true>(P.g, item); break;
-    case C_FOLD + 7: fold_item<2, int32_t, int64_t, M_FINAL_U, false, true>(P.g, item); break;
-    case C_FOLD + 8:
-      if constexpr (JMAX >= 3) fold_item<3, int16_t, int32_t, M_STORE, false, true>(P.g, item);
+    case C_FOLD + 0: fold_item<1, int16_t, int32_t, M_STORE, false, true, false>(P.g, item); break;
+    case C_FOLD + 1: fold_item<1, int16_t, int64_t, M_FINAL_U, false, true, false>(P.g, item); break;
+    case C_FOLD + 2: fold_item<1, int32_t, int32_t, M_STORE, false, true, false>(P.g, item); break;
+    case C_FOLD + 3: fold_item<1, int32_t, int64_t, M_FINAL_U, false, true, false>(P.g, item); break;
+    case C_FOLD + 4: fold_item<1, int16_t, int32_t, M_STORE, false, false, true>(P.g, item); break;
+    case C_FOLD + 5: fold_item<1, int16_t, int64_t, M_FINAL_U, false, false, true>(P.g, item); break;
+    case C_FOLD + 6: fold_item<1, int32_t, int32_t, M_STORE, false, false, true>(P.g, item); break;
+    case C_FOLD + 7: fold_item<1, int32_t, int64_t, M_FINAL_U, false, false, true>(P.g, item); break;
+    case C_FOLD + 8: fold_item<2, int16_t, int32_t, M_STORE, false, true, false>(P.g, item); break;
+    case C_FOLD + 9: fold_item<2, int16_t, int64_t, M_FINAL_U, false, true, false>(P.g, item); break;
+    case C_FOLD + 10: fold_item<2, int32_t, int32_t, M_STORE, false, true, false>(P.g, item); break;
+    case C_FOLD + 11: fold_item<2, int32_t, int64_t, M_FINAL_U, false, true, false>(P.g, item); break;
+    case C_FOLD + 12: fold_item<2, int16_t, int32_t, M_STORE, false, false, true>(P.g, item); break;
+    case C_FOLD + 13: fold_item<2, int16_t, int64_t, M_FINAL_U, false, false, true>(P.g, item); break;
+    case C_FOLD + 14: fold_item<2, int32_t, int32_t, M_STORE, false, false, true>(P.g, item); break;
+    case C_FOLD + 15: fold_item<2, int32_t, int64_t, M_FINAL_U, false, false, true>(P.g, item); break;
+    case C_FOLD + 16:
+      if constexpr (JMAX >= 3) fold_item<3, int16_t, int32_t, M_STORE, false, true, false>(P.g, item);
       break;
-    case C_FOLD + 9:
-      if constexpr (JMAX >= 3) fold_item<3, int16_t, int64_t, M_FINAL_U, false, true>(P.g, item);
+    case C_FOLD + 17:
+      if constexpr (JMAX >= 3) fold_item<3, int16_t, int64_t, M_FINAL_U, false, true, false>(P.g, item);
       break;
-    case C_FOLD + 10:
-      if constexpr (JMAX >= 3) fold_item<3, int32_t, int32_t, M_STORE, false, true>(P.g, item);
+    case C_FOLD + 18:
+      if constexpr (JMAX >= 3) fold_item<3, int32_t, int32_t, M_STORE, false, true, false>(P.g, item);
       break;
-    case C_FOLD + 11:
-      if constexpr (JMAX >= 3) fold_item<3, int32_t, int64_t, M_FINAL_U, false, true>(P.g, item);
+    case C_FOLD + 19:
+      if constexpr (JMAX >= 3) fold_item<3, int32_t, int64_t, M_FINAL_U, false, true, false>(P.g, item);
+      break;
+    case C_FOLD + 20:
+      if constexpr (JMAX >= 3) fold_item<3, int16_t, int32_t, M_STORE, false, false, true>(P.g, item);
+      break;
+    case C_FOLD + 21:
+      if constexpr (JMAX >= 3) fold_item<3, int16_t, int64_t, M_FINAL_U, false, false, true>(P.g, item);
+      break;
+    case C_FOLD + 22:
+      if constexpr (JMAX >= 3) fold_item<3, int32_t, int32_t, M_STORE, false, false, true>(P.g, item);
+      break;
+    case C_FOLD + 23:
+      if constexpr (JMAX >= 3) fold_item<3, int32_t, int64_t, M_FINAL_U, false, false, true>(P.g, item);
       break;
     case C_ASM + 0: asm_item<NumI64, 1, false, false>(P.a, item); break;
     case C_ASM + 1: asm_item<NumI64, 1, false, true>(P.a, item); break;
@@ -200,7 +220,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
     for (size_t k = 0; k < fp.size(); ++k) {
       BPhase b{};
       const P0 &q = fp[k];
-      b.code = C_FOLD + (q.J - 1) * 4 + (q.in16 ? 0 : 2) + (q.last ? 1 : 0);
+      b.code = C_FOLD + (q.J - 1) * 8 + (k == 0 ? 4 : 0) + (q.in16 ? 0 : 2) + (q.last ? 1 : 0);
       GenParams &g = b.g;
       g.in = in;
       g.out = q.last ? static_cast<void *>(I.theta) : static_cast<void *>(k % 2 == 0 ? A : Bf);

@@ -92,8 +92,41 @@ __device__ __forceinline__ T ld_in(const T *p) {
   else return __ldg(p);
 }
 
-// One output column (ah, oh, c) of a fold pass.
-template <int J, typename InT, typename AccT, int MODE, bool WEIGHT, bool COHERENT = false>
+// The 2^J contiguous counts of one basis row (first pass, C == 1) as vector
+// loads on the read-only path (counts are never written by the kernels).
+template <int NO, typename InT, typename V>
+__device__ __forceinline__ void ld_row_vec(const InT *p, V (&v)[NO]) {
+  constexpr int BYTES = NO * (int)sizeof(InT);
+  if constexpr (BYTES == 32) {
+    const int4 a = __ldg(reinterpret_cast<const int4 *>(p));
+    const int4 b = __ldg(reinterpret_cast<const int4 *>(p) + 1);
+    const int w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < NO; ++k) v[k] = (V)w[k];
+  } else {
+    uint32_t w[4];
+    if constexpr (BYTES == 16) {
+      const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+      w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    } else if constexpr (BYTES == 8) {
+      const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
+      w[0] = a.x; w[1] = a.y;
+    } else {
+      w[0] = __ldg(reinterpret_cast<const uint32_t *>(p));
+    }
+#pragma unroll
+    for (int k = 0; k < NO; ++k) {
+      if constexpr (sizeof(InT) == 2)
+        v[k] = (V)(int16_t)(uint16_t)(w[k >> 1] >> (16 * (k & 1)));
+      else
+        v[k] = (V)(int32_t)w[k];
+    }
+  }
+}
+
+// One output column (ah, oh, c) of a fold pass.  VEC: first pass (C == 1),
+// the row's 2^J outcomes loaded as one vector.
+template <int J, typename InT, typename AccT, int MODE, bool WEIGHT, bool COHERENT = false, bool VEC = false>
 __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
   constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
   constexpr int NO = 1 << J;
@@ -120,8 +153,12 @@ __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += (double)v[m] * w;
     } else {
       AccT v[NO];
+      if constexpr (VEC) {
+        ld_row_vec<NO>(in + base + al * row_stride, v);
+      } else {
 #pragma unroll
-      for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)ld_in<COHERENT>(in + base + al * row_stride + ol * P.C);
+        for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)ld_in<COHERENT>(in + base + al * row_stride + ol * P.C);
+      }
       wht<J>(v);
 #pragma unroll
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
