@@ -46,6 +46,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device=None):
+    """Slowest rank's value (every rank gets it); CPU tensors under gloo."""
+    import torch
+    import torch.distributed as dist
+    use_cpu = device is None or dist.get_backend() == "gloo"
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cpu" if use_cpu else device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_per_step):
+    """Units all ranks processed per second (each rank runs its own instance:
+    weak scaling, no data-path collective)."""
+    return units_per_rank * world / (ms_per_step / 1000.0)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -301,13 +317,11 @@ def run_ours(args, wl):
     launches = lre.lre_launch_count(ctx) - launches0
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, device)
         dist.barrier()
     ms = total_ms / args.steps
     B = 3 ** n
-    value = B * world / (ms / 1000.0)
+    value = whole_job_rate(B, world, ms)
 
     per = {}
     for name, t in recs:
