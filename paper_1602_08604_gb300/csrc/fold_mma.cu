@@ -14,20 +14,23 @@
 // Exactness: each count c < 1024 becomes the fp16 1024 + c by one OR per
 // pair (0x6400 | c is the fp16 bit pattern of 1024 + c).  The bias adds
 // 1024 * sum_k Tt[plA][k] to D, which is 1024 * 216 for plA = III and zero
-// otherwise (a row of T sums to 6 for I and 0 for X, Y, Z); it is subtracted
-// in the epilogue.  Every partial sum stays below 2^24, so FP32 accumulation
+// otherwise (a row of T sums to 6 for I and 0 for X, Y, Z); the level-B
+// warps subtract it.  Every partial sum stays below 2^24, so FP32 accumulation
 // in TMEM is exact and D is the same integer the ALU path computes.
 //
 // Roles (192 threads):
 //   warp 0    TMA producer into a ring of R sub-tile slots (82 rows: one
-//             zero row after each tile so the padded 14th K-step reads 0 x 0)
-//   warp 1    converts a slot in place, issues 14 MMAs (M=128 with rows
-//             64..127 of A zero, N=24, K=16 each) into one of two TMEM
-//             accumulators and commits to an mbarrier
-//   warps 4,5 epilogue: tcgen05.ld of TMEM lanes 0..63 (plA), exact int32,
-//             into the level-B exchange buffer
-//   warps 2,3 level B on the ALU, as in the FWHT path
-// Every ring has one in-order consumer, so parity waits cannot alias, and
+//             zero row after each sub-tile so the padded 14th K-step reads
+//             0 x 0); a slot is released by a tcgen05.commit as soon as the
+//             MMAs reading it have completed
+//   warps 2,3 convert the slots in place (even / odd sub-tiles)
+//   warp 1    issues 14 MMAs per sub-tile (M=128 with rows 64..127 of A zero,
+//             N=24, K=16) into the sub-tile's 24 columns of a whole-tile
+//             accumulator in TMEM (216 columns, two tile buffers)
+//   warps 4,5 level B straight from TMEM: thread plA (TMEM lane) reads its
+//             216 columns eight at a time with tcgen05.ld, removes the bias,
+//             contracts the next three qubits on the ALU and writes 64 outputs
+// Every barrier has one in-order consumer, so parity waits cannot alias, and
 // every wait is bounded by time.
 #include <cuda_runtime.h>
 
@@ -45,18 +48,16 @@ namespace {
 using namespace passes;
 
 constexpr int MMA_THREADS = 192;
-constexpr int MMA_R = 4;                      // ring slots
+constexpr int MMA_R = 14;                     // ring slots (even: slot parity = converter)
 constexpr int SLOT_ROWS = 82;                 // 81 + one zero row
 constexpr int SLOT_BYTES = SLOT_ROWS * 128;   // int16 rows of 64 outcomes
 constexpr int A_BYTES = 16 * 28 * 128;        // 128 x 224 fp16, core-matrix layout
-constexpr int ZS = 217;                       // level-B exchange stride (odd)
-constexpr int ZW = 64 * ZS;
 constexpr int OFF_A = MMA_R * SLOT_BYTES;
-constexpr int OFF_Z = OFF_A + A_BYTES;
-constexpr int OFF_BAR = OFF_Z + 2 * ZW * 4;
-constexpr int MMA_SMEM = OFF_BAR + 32 * 8 + 1024;
+constexpr int OFF_BAR = OFF_A + A_BYTES;
+constexpr int MMA_SMEM = OFF_BAR + 64 * 8 + 1024;
 constexpr int BIAS = 1024 * 216;
-constexpr uint32_t TMEM_COLS = 64;
+constexpr uint32_t TMEM_COLS = 512;           // two whole-tile accumulators of 216 columns
+constexpr uint32_t TILE_COLS = 256;
 
 __global__ void __launch_bounds__(MMA_THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap tmap, const uint4 *__restrict__ gA,
@@ -65,14 +66,12 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *ring = smem;
   uint8_t *Am = smem + OFF_A;
-  int32_t *Z = reinterpret_cast<int32_t *>(smem + OFF_Z);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
-  uint64_t *empty = full + MMA_R;
-  uint64_t *mma_done = empty + MMA_R;
-  uint64_t *acc_free = mma_done + 2;
-  uint64_t *zfull = acc_free + 2;
-  uint64_t *zempty = zfull + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(zempty + 2);
+  uint64_t *conv = full + MMA_R;
+  uint64_t *empty = conv + MMA_R;
+  uint64_t *tile_done = empty + MMA_R;
+  uint64_t *tile_free = tile_done + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tile_free + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_oh = (1ll << n) >> 6;
@@ -84,13 +83,12 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < MMA_R; ++i) {
       sm103::mbar_init(&full[i], 1);
-      sm103::mbar_init(&empty[i], 64);
+      sm103::mbar_init(&conv[i], 32);
+      sm103::mbar_init(&empty[i], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      sm103::mbar_init(&mma_done[b], 1);
-      sm103::mbar_init(&acc_free[b], 64);
-      sm103::mbar_init(&zfull[b], 9 * 64);
-      sm103::mbar_init(&zempty[b], 64);
+      sm103::mbar_init(&tile_done[b], 1);
+      sm103::mbar_init(&tile_free[b], 64);
     }
     *abort_flag = 0;
     sm103::fence_barrier_init();
@@ -127,11 +125,10 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
         for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
           if (sm103::mbar_try_wait(&full[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
     }
-  } else if (warp == 1) {
-    const uint32_t idesc = sm103::umma_idesc_f16(128, 24);
-    const uint32_t a_base = sm103::smem_addr(Am);
-    int64_t g = 0;
-    for (; g < total; ++g) {
+  } else if (warp == 2 || warp == 3) {
+    // converters: warp 2 takes even sub-tiles, warp 3 odd ones (MMA_R even,
+    // so each slot always belongs to the same converter)
+    for (int64_t g = warp - 2; g < total; g += 2) {
       const int slot = (int)(g % MMA_R);
       if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
         give_up();
@@ -144,22 +141,38 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
         rows[k] = v;
       }
       sm103::fence_proxy_async_smem();
-      __syncwarp();
-      const int b = (int)(g & 1);
-      if (g >= 2 && !sm103::mbar_wait(&acc_free[b], (uint32_t)(((g >> 1) - 1) & 1), abort_flag)) {
+      sm103::mbar_arrive(&conv[slot]);
+    }
+  } else if (warp == 1) {
+    const uint32_t idesc = sm103::umma_idesc_f16(128, 24);
+    const uint32_t a_base = sm103::smem_addr(Am);
+    int64_t g = 0;
+    for (; g < total; ++g) {
+      const int slot = (int)(g % MMA_R);
+      const int64_t lt = g / 9;
+      const int s = (int)(g - lt * 9);
+      const int tb = (int)(lt & 1);
+      if (!sm103::mbar_wait(&conv[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+        give_up();
+        break;
+      }
+      if (s == 0 && lt >= 2 &&
+          !sm103::mbar_wait(&tile_free[tb], (uint32_t)(((lt >> 1) - 1) & 1), abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
       if (lane == 0) {
         const uint32_t b_base = sm103::smem_addr(ring + slot * SLOT_BYTES);
+        const uint32_t d = tmem + tb * TILE_COLS + s * 24;
 #pragma unroll 1
         for (int kk = 0; kk < 14; ++kk) {
           const uint64_t ad = sm103::umma_desc(a_base + kk * 256, 128, 28 * 128);
           const uint64_t bd = sm103::umma_desc(b_base + kk * 256, 128, 27 * 128);
-          sm103::umma_f16(tmem + b * 32, ad, bd, idesc, kk > 0);
+          sm103::umma_f16(d, ad, bd, idesc, kk > 0);
         }
-        sm103::umma_commit(&mma_done[b]);
+        sm103::umma_commit(&empty[slot]);                  // slot reusable when these finish
+        if (s == 8) sm103::umma_commit(&tile_done[tb]);    // whole tile accumulated
       }
       __syncwarp();
     }
@@ -167,66 +180,38 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     if (lane == 0 && g > 0) {
       const int64_t q = g - 1;
       for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
-        if (sm103::mbar_try_wait(&mma_done[q & 1], (uint32_t)((q >> 1) & 1))) break;
+        if (sm103::mbar_try_wait(&empty[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
     }
-  } else if (warp >= 4) {
-    const int plA = (warp - 4) * 32 + lane;  // TMEM lane quarter of warps 4, 5
-    for (int64_t g = 0; g < total; ++g) {
-      const int b = (int)(g & 1);
-      if (!sm103::mbar_wait(&mma_done[b], (uint32_t)((g >> 1) & 1), abort_flag)) {
+  } else {
+    // warps 4, 5: level B from TMEM lanes 0..63
+    const int plA = (warp - 4) * 32 + lane;
+    for (int64_t lt = 0; lt < my_tiles; ++lt) {
+      const int tb = (int)(lt & 1);
+      if (!sm103::mbar_wait(&tile_done[tb], (uint32_t)((lt >> 1) & 1), abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
-      uint32_t r[24];
-      const uint32_t ta = tmem + ((uint32_t)((warp - 4) * 32) << 16) + b * 32;
-      sm103::tmem_ld8(ta + 0, *reinterpret_cast<uint32_t(*)[8]>(r + 0));
-      sm103::tmem_ld8(ta + 8, *reinterpret_cast<uint32_t(*)[8]>(r + 8));
-      sm103::tmem_ld8(ta + 16, *reinterpret_cast<uint32_t(*)[8]>(r + 16));
-      sm103::tmem_ld_wait();
-      sm103::tc_fence_before();
-      sm103::mbar_arrive(&acc_free[b]);
-      sm103::mbar_arrive(&empty[g % MMA_R]);  // the MMAs reading the slot are done
-      const int64_t lt = g / 9;
-      const int s = (int)(g - lt * 9);
-      const int zb = (int)(lt & 1);
-      if (lt >= 2 && !sm103::mbar_wait(&zempty[zb], (uint32_t)(((lt >> 1) - 1) & 1), abort_flag)) {
-        give_up();
-        break;
-      }
-      int32_t *z = Z + zb * ZW + plA * ZS + s * 24;
-#pragma unroll
-      for (int i = 0; i < 24; ++i) {
-        int32_t v = (int32_t)__uint_as_float(r[i]);
-        if (plA == 0) v -= BIAS;
-        z[i] = v;
-      }
-      sm103::mbar_arrive(&zfull[zb]);
-    }
-  } else {
-    const int tb = threadIdx.x - 64;  // warps 2, 3: level B
-    for (int64_t lt = 0; lt < my_tiles; ++lt) {
-      const int64_t tile = blockIdx.x + lt * gridDim.x;
-      const int zb = (int)(lt & 1);
-      if (!sm103::mbar_wait(&zfull[zb], (uint32_t)((lt >> 1) & 1), abort_flag)) {
-        give_up();
-        break;
-      }
-      const int32_t *z = Z + zb * ZW;
+      const uint32_t ta = tmem + ((uint32_t)((warp - 4) * 32) << 16) + tb * TILE_COLS;
       int32_t acc[64];
 #pragma unroll
       for (int p = 0; p < 64; ++p) acc[p] = 0;
 #pragma unroll
       for (int alB = 0; alB < 27; ++alB) {
+        uint32_t r[8];
+        sm103::tmem_ld8(ta + alB * 8, r);
+        sm103::tmem_ld_wait();
         int32_t v[8];
 #pragma unroll
-        for (int olB = 0; olB < 8; ++olB) v[olB] = z[tb * ZS + alB * 8 + olB];
+        for (int i = 0; i < 8; ++i) v[i] = (int32_t)__uint_as_float(r[i]) - (plA == 0 ? BIAS : 0);
         wht<3>(v);
 #pragma unroll
         for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
       }
-      sm103::mbar_arrive(&zempty[zb]);
-      int32_t *o = out + tile * 4096 + tb;
+      sm103::tc_fence_before();
+      sm103::mbar_arrive(&tile_free[tb]);
+      const int64_t tile = blockIdx.x + lt * gridDim.x;
+      int32_t *o = out + tile * 4096 + plA;
 #pragma unroll
       for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
     }
