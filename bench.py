@@ -133,13 +133,22 @@ def source_digest(paths):
     return h.hexdigest()[:16]
 
 
+# sources whose digest pins a recorded DRAM traffic figure to the kernel it was taken on
+KERNEL_SOURCES = {
+    "fold_first6": ["paper_1602_08604_gb300/csrc/fold.cu", "paper_1602_08604_gb300/csrc/passes.cuh",
+                    "paper_1602_08604_gb300/csrc/sm103.cuh"],
+    "fold_first6_mma": ["paper_1602_08604_gb300/csrc/fold_mma.cu", "paper_1602_08604_gb300/csrc/passes.cuh",
+                        "paper_1602_08604_gb300/csrc/sm103.cuh"],
+}
+
+
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch from profiles/traffic.txt when the kernel's
     sources are unchanged since the capture; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
-    digest = source_digest(["paper_1602_08604_gb300/csrc/fold.cu"])
+    digest = source_digest(KERNEL_SOURCES[kernel])
     with open(p) as f:
         for line in f:
             parts = line.split()
@@ -286,8 +295,7 @@ def run_ours(args, wl):
     theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
     rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
     ctx = lre.lre_create(local)
-    if args.fold_path == "tensor":
-        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+    lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if args.fold_path == "tensor" else lre.LRE_FOLD_FWHT)
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -530,8 +538,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--project", action="store_true", help="also time step (iii) once")
-    ap.add_argument("--fold-path", default="fwht", choices=["fwht", "tensor"],
-                    help="first fold pass on the ALUs (FWHT) or on the tensor cores")
+    ap.add_argument("--fold-path", default="tensor", choices=["fwht", "tensor"],
+                    help="first fold pass on the tensor cores (the library default) or on the ALUs (FWHT)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     args = ap.parse_args()

@@ -199,17 +199,19 @@ lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre
 lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream,
                           float *best_ms);
 
-/* First fold pass of step (i) on later calls of this context:
- * LRE_FOLD_FWHT (default): the parity transform (Walsh-Hadamard butterflies)
- *   and the ternary fold on the integer ALUs;
- * LRE_FOLD_TENSOR: the same contraction of the first three qubits as a GEMM
- *   on the 5th-generation tensor cores (tcgen05.mma kind::f16 with FP32
- *   accumulation in TMEM) against the constant +-1/0 matrix of Sec. III's
- *   per-qubit Gamma structure, exact because every count is an fp16 integer
- *   and every partial sum stays below 2^24 (bit-identical to FWHT).  It
- *   applies to int16 counts with shots per basis (hence every count) below
- *   1024; other calls run the FWHT path.  The first switch to TENSOR
- *   allocates a 56 KiB operand buffer in the context. */
+/* First fold pass of step (i) (the first six qubits) on later calls of this
+ * context:
+ * LRE_FOLD_TENSOR (default): the level-A contraction of each 729 x 64 count
+ *   tile is a GEMM on the 5th-generation tensor cores (tcgen05.mma kind::f16,
+ *   FP32 accumulation in TMEM) against the constant +-1/0 matrix of the
+ *   per-qubit map of Sec. III / Eq. 3: the int16 count c is read unchanged as
+ *   the fp16 bit pattern of c * 2^-24, exact for c < 2048, and every partial
+ *   sum stays below 2^24 units, so the result is bit-identical to the FWHT
+ *   path.  It applies to int16 counts whose per-basis shot number (hence
+ *   every count) is at most 2047, with uniform shots; every other call runs
+ *   the FWHT path.
+ * LRE_FOLD_FWHT: the parity transform (Walsh-Hadamard butterflies) and the
+ *   ternary fold on the integer ALUs, for every input. */
 #define LRE_FOLD_FWHT 0
 #define LRE_FOLD_TENSOR 1
 lre_status lre_set_fold_path(lre_ctx *ctx, int path);

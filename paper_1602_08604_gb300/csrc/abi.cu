@@ -145,8 +145,15 @@ lre_status lre_create(lre_ctx **out, int device) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->mma_operand, lre::mma_operand_bytes());
   if (e != cudaSuccess) {
     lre_status st = cuda_fail(ctx, e, "lre_create");
+    lre_destroy(ctx);
+    return st;
+  }
+  lre_status st = lre::mma_operand_upload(ctx, ctx->mma_operand, nullptr);
+  if (st == LRE_OK && (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) st = cuda_fail(ctx, e, "lre_create");
+  if (st != LRE_OK) {
     lre_destroy(ctx);
     return st;
   }
@@ -332,11 +339,20 @@ uint64_t lre_launch_count(lre_ctx *ctx) { return ctx ? ctx->launches : 0; }
 }  // extern "C"
 
 // Test hook (not part of include/lre.h): choose the first fold pass of later
-// calls on this context: 0 register kernel, 1 TMA pipeline, 2 TMA pipeline
-// fused with the second pass where the plan allows (the default).
+// calls on this context: 0 register kernel, 1 TMA pipeline (the default), 2
+// TMA pipeline fused with the second pass where the plan allows.
 extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   if (!ctx || variant < 0 || variant > 2) return LRE_ERR_INVALID_ARG;
   ctx->first_variant = variant;
+  return LRE_OK;
+}
+
+// Test hook (not part of include/lre.h): operand encoding of the tensor-core
+// first pass: 0 counts below 2048 used as fp16 bit patterns (the default), 1
+// counts below 1024 converted to fp16(1024 + c) in shared memory.
+extern "C" lre_status lre_debug_set_mma_variant(lre_ctx *ctx, int biased) {
+  if (!ctx || biased < 0 || biased > 1) return LRE_ERR_INVALID_ARG;
+  ctx->mma_biased = biased;
   return LRE_OK;
 }
 
@@ -357,19 +373,6 @@ extern "C" lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, in
 
 extern "C" lre_status lre_set_fold_path(lre_ctx *ctx, int path) {
   if (!ctx || (path != LRE_FOLD_FWHT && path != LRE_FOLD_TENSOR)) return LRE_ERR_INVALID_ARG;
-  lre_status st = set_device(ctx);
-  if (st != LRE_OK) return st;
-  if (path == LRE_FOLD_TENSOR && !ctx->mma_operand) {
-    cudaError_t e = cudaMalloc(&ctx->mma_operand, lre::mma_operand_bytes());
-    if (e != cudaSuccess) {
-      ctx->mma_operand = nullptr;
-      cudaGetLastError();
-      return lre::cuda_fail(ctx, e, "tensor-core operand");
-    }
-    if ((st = lre::mma_operand_upload(ctx, ctx->mma_operand, nullptr)) != LRE_OK) return st;
-    e = cudaStreamSynchronize(nullptr);
-    if (e != cudaSuccess) return lre::cuda_fail(ctx, e, "tensor-core operand");
-  }
   ctx->fold_path = path;
   return LRE_OK;
 }

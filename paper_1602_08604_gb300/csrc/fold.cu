@@ -450,13 +450,14 @@ EncodeTiled encode_fn() {
 }
 
 // TMA map over rows [0, rows) of a [rows][2^n] count matrix, box 81 x 64.
-bool make_count_map(CUtensorMap *map, const void *base, lre_count_kind kind, int n, int64_t rows) {
+bool make_count_map(CUtensorMap *map, const void *base, lre_count_kind kind, int n, int64_t rows,
+                    uint32_t box_rows = SUB_ROWS) {
   EncodeTiled enc = encode_fn();
   if (!enc) return false;
   const size_t es = kind == LRE_COUNTS_I16 ? 2 : 4;
   const cuuint64_t dims[2] = {(cuuint64_t)1 << n, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {((cuuint64_t)1 << n) * es};
-  const cuuint32_t box[2] = {64, SUB_ROWS};
+  const cuuint32_t box[2] = {64, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, kind == LRE_COUNTS_I16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_INT32,
                    2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -675,11 +676,14 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       out = (k % 2 == 0) ? bufA : bufB;
     else
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmap_tail;
     const bool tensor = pp.first6 && !pp.fused9 && ctx->fold_path == 1 && ctx->mma_operand &&
-                        pp.in_t == T_I16 && a.shots_uniform > 0 && a.shots_uniform < 1024;
-    if (tensor && make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r))) {
-      lre_status st = mma_first_pass(ctx, tmap, ctx->mma_operand, static_cast<int32_t *>(out), pp.r, s);
+                        pp.in_t == T_I16 && a.shots_uniform > 0 &&
+                        a.shots_uniform <= mma_max_count(ctx->mma_biased);
+    if (tensor && make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(0)) &&
+        make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
+      lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), pp.r,
+                                     ctx->mma_biased, s);
       if (st != LRE_OK) return st;
     } else if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
         make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {

@@ -1,37 +1,48 @@
-// Tensor-core form of the first fold pass (int16 counts below 1024).
+// Tensor-core form of the first fold pass (int16 counts below 2048).
 //
-// The level-A contraction of a sub-tile (81 basis rows x 64 outcomes, three
-// qubits in the rows and three in the outcome octets) is the GEMM
-//     D[plA][item] = sum_k Tt[plA][k] X[k][item],   k = (alA, olA), item = (a3, olB)
+// A tile is 729 basis rows x 64 outcomes: six qubits in the rows (alB: the
+// high three, alA: the low three) and six in the outcomes (olB, olA).  Its
+// level-A contraction is the GEMM
+//     D[plA][(alB, olB)] = sum_k Tt[plA][k] X[(alB, olB)][k],   k = (alA, olA)
 // with Tt the constant 64 x 216 matrix of the per-qubit map T (entries 0, +1,
 // -1).  In the K-major canonical layout of the tensor-core operands a core
 // matrix is 8 rows x 16 bytes; for X those 8 rows are the 8 outcome octets
-// (olB) of one basis row and the 16 bytes are the octet's 8 counts (olA), i.e.
-// a core matrix is exactly one 128-byte count row of the TMA tile.  So the
-// tile feeds tcgen05.mma (kind::f16) where it landed: K-step stride
-// (next alA) = 128 B, N-group stride (next a3) = 27 rows.
+// (olB) of one basis row and the 16 bytes the octet's 8 counts (olA), so a
+// core matrix is exactly one 128-byte count row as TMA lands it: the K-step
+// stride (next alA) is one row and the N-group stride (next alB) 27 rows, the
+// same for every alB of the tile.  The tile therefore feeds two MMA chains in
+// place, N = 128 (alB 0..15) and N = 96 (alB 16..27; alB 27 reads rows past
+// the tile and lands in accumulator columns nobody reads).
 //
-// Exactness: each count c < 1024 becomes the fp16 1024 + c by one OR per
-// pair (0x6400 | c is the fp16 bit pattern of 1024 + c).  The bias adds
-// 1024 * sum_k Tt[plA][k] to D, which is 1024 * 216 for plA = III and zero
-// otherwise (a row of T sums to 6 for I and 0 for X, Y, Z); the level-B
-// warps subtract it.  Every partial sum stays below 2^24, so FP32 accumulation
-// in TMEM is exact and D is the same integer the ALU path computes.
+// K = 216 is 13.5 K-steps of 16: the 14th step reads rows alA = 25, 26 against
+// an operand column block that is zero for alA = 25, so no row outside an alB
+// group enters a used column.
 //
-// Roles (192 threads):
-//   warp 0    TMA producer into a ring of R sub-tile slots (82 rows: one
-//             zero row after each sub-tile so the padded 14th K-step reads
-//             0 x 0); a slot is released by a tcgen05.commit as soon as the
-//             MMAs reading it have completed
-//   warps 2,3 convert the slots in place (even / odd sub-tiles)
-//   warp 1    issues 14 MMAs per sub-tile (M=128 with rows 64..127 of A zero,
-//             N=24, K=16) into the sub-tile's 24 columns of a whole-tile
-//             accumulator in TMEM (216 columns, two tile buffers)
-//   warps 4,5 level B straight from TMEM: thread plA (TMEM lane) reads its
-//             216 columns eight at a time with tcgen05.ld, removes the bias,
-//             contracts the next three qubits on the ALU and writes 64 outputs
-// Every barrier has one in-order consumer, so parity waits cannot alias, and
-// every wait is bounded by time.
+// Operand encoding, two variants:
+//   RAW      the int16 count c < 2048 is used unchanged as fp16 bits, which
+//            encode exactly c * 2^-24 (subnormal below 1024, the first
+//            binade above); D = S * 2^-24.
+//   BIASED   a converter pass ORs 0x6400 into each count (c < 1024), giving
+//            fp16(1024 + c); D = S + 1024 * rowsum(Tt) = S + 1024 * 216 for
+//            plA = III and S otherwise.
+// Every partial sum is an integer multiple of the smallest unit below 2^24
+// units, so FP32 accumulation in TMEM is exact and the level-B warps recover
+// the same integer the ALU path computes.
+//
+// Roles (256 threads, one CTA per SM):
+//   warp 0     TMA producer into a ring of 3 chunk slots (one chunk = 16 alB
+//              groups = 432 rows); a slot is released by tcgen05.commit once
+//              the MMAs reading it have completed
+//   warp 1     issues 14 MMAs (M = 128, K = 16) per chunk into the tile's
+//              accumulator (224 columns; two tile buffers in 512 columns)
+//   warps 2,3  BIASED only: convert each chunk in place (half the rows each)
+//   warps 4,5  level B of even tiles from TMEM lanes 0..63
+//   warps 6,7  level B of odd tiles from TMEM lanes 64..127 (rows 64..127 of
+//              the operand repeat Tt, so those lanes hold the same D)
+// Level B: thread plA reads its 216 columns 32 at a time, contracts the next
+// three qubits (alB, olB) on the ALU and writes 64 outputs.  Every barrier has
+// in-order consumers only, so parity waits cannot alias, and every wait is
+// bounded by time.
 #include <cuda_runtime.h>
 
 #include <cudaTypedefs.h>
@@ -47,25 +58,37 @@ namespace {
 
 using namespace passes;
 
-constexpr int MMA_THREADS = 192;
-constexpr int MMA_R = 14;                     // ring slots (even: slot parity = converter)
-constexpr int SLOT_ROWS = 82;                 // 81 + one zero row
-constexpr int SLOT_BYTES = SLOT_ROWS * 128;   // int16 rows of 64 outcomes
-constexpr int A_BYTES = 16 * 28 * 128;        // 128 x 224 fp16, core-matrix layout
-constexpr int OFF_A = MMA_R * SLOT_BYTES;
-constexpr int OFF_BAR = OFF_A + A_BYTES;
-constexpr int MMA_SMEM = OFF_BAR + 64 * 8 + 1024;
+constexpr int MMA_THREADS = 256;
+constexpr int MMA_R = 3;                       // ring slots of one chunk each
+constexpr int CHUNK_ROWS = 432;                // 16 alB groups x 27 rows
+constexpr int SLOT_BYTES = CHUNK_ROWS * 128;   // int16 rows of 64 outcomes
+constexpr int A_BYTES = 16 * 28 * 128;         // 128 x 224 fp16, core-matrix layout
+constexpr int OFF_RING = A_BYTES;
+constexpr int OFF_BAR = OFF_RING + MMA_R * SLOT_BYTES;
+constexpr int MMA_SMEM = OFF_BAR + 32 * 8 + 1024;
 constexpr int BIAS = 1024 * 216;
-constexpr uint32_t TMEM_COLS = 512;           // two whole-tile accumulators of 216 columns
+constexpr uint32_t TMEM_COLS = 512;            // two tile accumulators
 constexpr uint32_t TILE_COLS = 256;
+constexpr uint32_t BOX_BIG = 216, BOX_TAIL = 81;  // TMA boxes: 8 and 3 alB groups
+static_assert(MMA_SMEM <= 232448, "shared memory of one CTA");
+static_assert(2 * BOX_BIG <= CHUNK_ROWS && BOX_BIG + BOX_TAIL <= CHUNK_ROWS, "chunk fits its slot");
+// the N = 96 chain reads alB = 27 (rows 729..755 of the tile): still inside the slot
+static_assert(12 * 27 <= CHUNK_ROWS, "padded alB group stays in the slot");
 
+__device__ __forceinline__ int32_t d_to_int(uint32_t bits, float scale, int32_t sub) {
+  // x * scale is an integer of magnitude below 2^22; adding 1.5 * 2^23 puts it
+  // in the low mantissa bits
+  return __float_as_int(fmaf(__uint_as_float(bits), scale, 12582912.f)) - 0x4B400000 - sub;
+}
+
+template <bool BIASED>
 __global__ void __launch_bounds__(MMA_THREADS, 1)
-    fold_first6_mma(const __grid_constant__ CUtensorMap tmap, const uint4 *__restrict__ gA,
-                    int32_t *__restrict__ out, int n, int64_t tiles, int *status) {
+    fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
+                    const uint4 *__restrict__ gA, int32_t *__restrict__ out, int n, int64_t tiles, int *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
-  uint8_t *ring = smem;
-  uint8_t *Am = smem + OFF_A;
+  uint8_t *Am = smem;
+  uint8_t *ring = smem + OFF_RING;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
   uint64_t *conv = full + MMA_R;
   uint64_t *empty = conv + MMA_R;
@@ -76,14 +99,11 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_oh = (1ll << n) >> 6;
 
-  // constant operand A and the zero pad rows
   for (int i = threadIdx.x; i < A_BYTES / 16; i += MMA_THREADS) reinterpret_cast<uint4 *>(Am)[i] = gA[i];
-  for (int i = threadIdx.x; i < MMA_R * 8; i += MMA_THREADS)
-    reinterpret_cast<uint4 *>(ring + (i >> 3) * SLOT_BYTES + 81 * 128)[i & 7] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     for (int i = 0; i < MMA_R; ++i) {
       sm103::mbar_init(&full[i], 1);
-      sm103::mbar_init(&conv[i], 32);
+      sm103::mbar_init(&conv[i], 64);
       sm103::mbar_init(&empty[i], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -93,7 +113,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     *abort_flag = 0;
     sm103::fence_barrier_init();
   }
-  sm103::fence_proxy_async_smem();  // A and the pad rows are read by the tensor cores
+  sm103::fence_proxy_async_smem();  // A is read by the tensor cores
   if (warp == 1) sm103::tmem_alloc(tmem_slot, TMEM_COLS);
   sm103::tc_fence_before();
   __syncthreads();
@@ -104,75 +124,64 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     latch(status, LRE_ERR_TIMEOUT);
   };
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const int64_t total = my_tiles * 9;  // sub-tiles of this CTA
+  const int64_t total = my_tiles * 2;  // chunks of this CTA
 
   if (warp == 0) {
     if (lane == 0) {
       int64_t g = 0;
       for (; g < total && !*abort_flag; ++g) {
-        const int64_t tile = blockIdx.x + (g / 9) * gridDim.x;
-        const int s = (int)(g % 9);
+        const int64_t tile = blockIdx.x + (g >> 1) * gridDim.x;
+        const int c = (int)(g & 1);
         const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
         const int slot = (int)(g % MMA_R);
         if (g >= MMA_R && !sm103::mbar_wait(&empty[slot], (uint32_t)((g / MMA_R - 1) & 1), abort_flag)) {
           give_up();
           break;
         }
-        sm103::mbar_arrive_expect_tx(&full[slot], 81 * 128);
-        sm103::tma_load_2d(ring + slot * SLOT_BYTES, &tmap, (int)(oh * 64), (int)(ah * 729 + s * 81), &full[slot]);
+        uint8_t *dst = ring + slot * SLOT_BYTES;
+        const int x = (int)(oh * 64), y = (int)(ah * 729 + c * 432);
+        sm103::mbar_arrive_expect_tx(&full[slot], (BOX_BIG + (c ? BOX_TAIL : BOX_BIG)) * 128);
+        sm103::tma_load_2d(dst, &map_big, x, y, &full[slot]);
+        if (c == 0)
+          sm103::tma_load_2d(dst + BOX_BIG * 128, &map_big, x, y + (int)BOX_BIG, &full[slot]);
+        else
+          sm103::tma_load_2d(dst + BOX_BIG * 128, &map_tail, x, y + (int)BOX_BIG, &full[slot]);
       }
       for (int64_t q = g > MMA_R ? g - MMA_R : 0; q < g; ++q)  // drain in-flight loads
         for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
           if (sm103::mbar_try_wait(&full[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
     }
-  } else if (warp == 2 || warp == 3) {
-    // converters: warp 2 takes even sub-tiles, warp 3 odd ones (MMA_R even,
-    // so each slot always belongs to the same converter)
-    for (int64_t g = warp - 2; g < total; g += 2) {
-      const int slot = (int)(g % MMA_R);
-      if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
-        give_up();
-        break;
-      }
-      uint4 *rows = reinterpret_cast<uint4 *>(ring + slot * SLOT_BYTES);
-      for (int k = lane; k < 81 * 8; k += 32) {  // counts -> fp16(1024 + c), in place
-        uint4 v = rows[k];
-        v.x |= 0x64006400u; v.y |= 0x64006400u; v.z |= 0x64006400u; v.w |= 0x64006400u;
-        rows[k] = v;
-      }
-      sm103::fence_proxy_async_smem();
-      sm103::mbar_arrive(&conv[slot]);
-    }
   } else if (warp == 1) {
-    const uint32_t idesc = sm103::umma_idesc_f16(128, 24);
     const uint32_t a_base = sm103::smem_addr(Am);
     int64_t g = 0;
     for (; g < total; ++g) {
       const int slot = (int)(g % MMA_R);
-      const int64_t lt = g / 9;
-      const int s = (int)(g - lt * 9);
+      const int64_t lt = g >> 1;
+      const int c = (int)(g & 1);
       const int tb = (int)(lt & 1);
-      if (!sm103::mbar_wait(&conv[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+      if (c == 0 && lt >= 2 &&
+          !sm103::mbar_wait(&tile_free[tb], (uint32_t)(((lt >> 1) - 1) & 1), abort_flag)) {
         give_up();
         break;
       }
-      if (s == 0 && lt >= 2 &&
-          !sm103::mbar_wait(&tile_free[tb], (uint32_t)(((lt >> 1) - 1) & 1), abort_flag)) {
+      if (!sm103::mbar_wait(BIASED ? &conv[slot] : &full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
       if (lane == 0) {
         const uint32_t b_base = sm103::smem_addr(ring + slot * SLOT_BYTES);
-        const uint32_t d = tmem + tb * TILE_COLS + s * 24;
+        const uint32_t d = tmem + tb * TILE_COLS + c * 128;
+        const uint32_t idesc = sm103::umma_idesc_f16(128, c ? 96 : 128);
 #pragma unroll 1
         for (int kk = 0; kk < 14; ++kk) {
+          const int brow = kk < 13 ? 2 * kk : 25;
           const uint64_t ad = sm103::umma_desc(a_base + kk * 256, 128, 28 * 128);
-          const uint64_t bd = sm103::umma_desc(b_base + kk * 256, 128, 27 * 128);
+          const uint64_t bd = sm103::umma_desc(b_base + brow * 128, 128, 27 * 128);
           sm103::umma_f16(d, ad, bd, idesc, kk > 0);
         }
-        sm103::umma_commit(&empty[slot]);                  // slot reusable when these finish
-        if (s == 8) sm103::umma_commit(&tile_done[tb]);    // whole tile accumulated
+        sm103::umma_commit(&empty[slot]);                 // slot reusable when these finish
+        if (c == 1) sm103::umma_commit(&tile_done[tb]);   // whole tile accumulated
       }
       __syncwarp();
     }
@@ -182,34 +191,63 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
       for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
         if (sm103::mbar_try_wait(&empty[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
     }
+  } else if (warp == 2 || warp == 3) {
+    if constexpr (BIASED) {
+      for (int64_t g = 0; g < total; ++g) {
+        const int slot = (int)(g % MMA_R);
+        if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+          give_up();
+          break;
+        }
+        const int rows = (g & 1) ? (int)(BOX_BIG + BOX_TAIL) : (int)(2 * BOX_BIG);
+        uint4 *v4 = reinterpret_cast<uint4 *>(ring + slot * SLOT_BYTES);
+#pragma unroll 4
+        for (int k = (warp - 2) * 32 + lane; k < rows * 8; k += 64) {  // counts -> fp16(1024 + c)
+          uint4 v = v4[k];
+          v.x |= 0x64006400u; v.y |= 0x64006400u; v.z |= 0x64006400u; v.w |= 0x64006400u;
+          v4[k] = v;
+        }
+        sm103::fence_proxy_async_smem();
+        sm103::mbar_arrive(&conv[slot]);
+      }
+    }
   } else {
-    // warps 4, 5: level B from TMEM lanes 0..63
-    const int plA = (warp - 4) * 32 + lane;
-    for (int64_t lt = 0; lt < my_tiles; ++lt) {
-      const int tb = (int)(lt & 1);
-      if (!sm103::mbar_wait(&tile_done[tb], (uint32_t)((lt >> 1) & 1), abort_flag)) {
+    // warps 4,5: even tiles, TMEM lanes 0..63; warps 6,7: odd tiles, lanes 64..127
+    const int pair = (warp - 4) >> 1;
+    const int quarter = warp & 3;
+    const int plA = (quarter & 1) * 32 + lane;
+    const float scale = BIASED ? 1.f : 16777216.f;
+    const int32_t sub = BIASED && plA == 0 ? BIAS : 0;
+    for (int64_t lt = pair; lt < my_tiles; lt += 2) {
+      if (!sm103::mbar_wait(&tile_done[pair], (uint32_t)((lt >> 1) & 1), abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)((warp - 4) * 32) << 16) + tb * TILE_COLS;
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + pair * TILE_COLS;
       int32_t acc[64];
 #pragma unroll
       for (int p = 0; p < 64; ++p) acc[p] = 0;
 #pragma unroll
-      for (int alB = 0; alB < 27; ++alB) {
-        uint32_t r[8];
-        sm103::tmem_ld8(ta + alB * 8, r);
+      for (int grp = 0; grp < 7; ++grp) {  // columns 32 grp .. 32 grp + 31: alB = 4 grp .. 4 grp + 3
+        uint32_t r[32];
+        sm103::tmem_ld32(ta + grp * 32, r);
         sm103::tmem_ld_wait();
-        int32_t v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = (int32_t)__uint_as_float(r[i]) - (plA == 0 ? BIAS : 0);
-        wht<3>(v);
+        for (int j = 0; j < 4; ++j) {
+          const int alB = grp * 4 + j;
+          if (alB < 27) {
+            int32_t v[8];
 #pragma unroll
-        for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
+            for (int i = 0; i < 8; ++i) v[i] = d_to_int(r[j * 8 + i], scale, sub);
+            wht<3>(v);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
+          }
+        }
       }
       sm103::tc_fence_before();
-      sm103::mbar_arrive(&tile_free[tb]);
+      sm103::mbar_arrive(&tile_free[pair]);
       const int64_t tile = blockIdx.x + lt * gridDim.x;
       int32_t *o = out + tile * 4096 + plA;
 #pragma unroll
@@ -224,44 +262,53 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   }
 }
 
-// Tt as fp16 bits in the K-major core-matrix layout: row plA (0..127, rows
-// 64.. zero), column k = alA*8 + olA (0..223, alA = 27 zero); core matrix
-// (m-group, k-group) at (m-group * 28 + k-group) * 128 bytes.
+// Tt as fp16 bits in the K-major core-matrix layout: row m (0..127) holds
+// plA = m mod 64; column k = j*8 + olA over K-groups j = 0..27, where groups
+// 0..25 are alA = j, group 26 is zero (it meets alA = 25 a second time in the
+// last K-step) and group 27 is alA = 26.  Core matrix (m-group, j) sits at
+// (m-group * 28 + j) * 128 bytes.
 std::vector<uint16_t> make_a_operand() {
   std::vector<uint16_t> A(A_BYTES / 2, 0);
   const uint16_t one = 0x3C00, mone = 0xBC00;
-  for (int p = 0; p < 64; ++p)
-    for (int al = 0; al < 27; ++al)
+  for (int m = 0; m < 128; ++m)
+    for (int j = 0; j < 28; ++j) {
+      if (j == 26) continue;
+      const int al = j < 26 ? j : 26;
       for (int ol = 0; ol < 8; ++ol) {
         int v = 1;
-        for (int q = 0, pp = p, aa = al; q < 3; ++q, pp >>= 2, aa /= 3) {
+        for (int q = 0, pp = m & 63, aa = al; q < 3; ++q, pp >>= 2, aa /= 3) {
           const int letter = pp & 3, axis = aa % 3, o = (ol >> q) & 1;
           if (letter == 0) continue;            // I: +1
           if (letter != axis + 1) { v = 0; break; }
           if (o) v = -v;                        // matching axis: (-1)^o
         }
         if (v == 0) continue;
-        const int k = al * 8 + ol;
-        const size_t idx = ((size_t)(p >> 3) * 28 + (k >> 3)) * 64 + (p & 7) * 8 + (k & 7);
+        const size_t idx = ((size_t)(m >> 3) * 28 + j) * 64 + (m & 7) * 8 + ol;
         A[idx] = v > 0 ? one : mone;
       }
+    }
   return A;
 }
 
 }  // namespace
 
 size_t mma_operand_bytes() { return A_BYTES; }
+uint32_t mma_box_rows(int which) { return which ? BOX_TAIL : BOX_BIG; }
+int64_t mma_max_count(int biased) { return biased ? 1023 : 2047; }
 
 // Launch the tensor-core first pass over all tiles of an n-qubit int16 count
-// matrix; a_dev must hold the operand written by mma_operand_upload.
-lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &tmap, const void *a_dev, int32_t *out, int n,
-                          cudaStream_t s) {
+// matrix.  map_big / map_tail are tensor maps of the counts with boxes of
+// 216 / 81 rows x 64 outcomes; a_dev holds the operand written by
+// mma_operand_upload; every count must be at most mma_max_count(biased).
+lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
+                          int32_t *out, int n, int biased, cudaStream_t s) {
   const int64_t tiles = ipow(3, n - 6) << (n - 6);
   const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
   Launch L(ctx, "fold_first6_mma", s);
-  cudaFuncSetAttribute(fold_first6_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
-  fold_first6_mma<<<grid, MMA_THREADS, MMA_SMEM, s>>>(tmap, static_cast<const uint4 *>(a_dev), out, n, tiles,
-                                                     ctx->d_status);
+  auto kern = biased ? fold_first6_mma<true> : fold_first6_mma<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
+  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, n, tiles,
+                                           ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }

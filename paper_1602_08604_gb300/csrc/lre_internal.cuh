@@ -36,8 +36,9 @@ struct lre_ctx {
   // pipeline fused with the second pass through L2 (correct, but slower on
   // GB300 so far: its second-pass jobs are L2-latency bound)
   int first_variant = 1;
-  int fold_path = 0;          // 0 FWHT on the ALU, 1 tensor cores for the first pass
+  int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores where the input allows
   void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
+  int mma_biased = 0;         // tensor-core operand: 0 raw counts as fp16 bits, 1 fp16(1024 + c)
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
   std::vector<char> batch_host;  // host copy of the last batched pass table
@@ -112,9 +113,11 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
 
 // ---- tensor-core first pass (fold_mma.cu) ----------------------------------------
 size_t mma_operand_bytes();
+uint32_t mma_box_rows(int which);    // TMA box rows: 0 the 216-row box, 1 the 81-row tail
+int64_t mma_max_count(int biased);   // largest count the operand encoding keeps exact
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
-lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &tmap, const void *a_dev, int32_t *out, int n,
-                          cudaStream_t s);
+lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
+                          int32_t *out, int n, int biased, cudaStream_t s);
 
 // ---- batched instances (one persistent launch) ---------------------------------
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);

@@ -56,6 +56,7 @@ def test_fused_second_pass_equals_unfused(n, dt):
         from synth import gen
         c = torch.empty((3 ** n, 2 ** n), dtype=torch.int16 if dt == np.int16 else torch.int32, device="cuda")
         gen.gen_ghz(n, 0.05, 1000, 77 + n, c)
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_FWHT)  # both sides on the ALU kernels
         res = []
         for variant in (1, 2):
             assert f(ctx, variant) == 0

@@ -33,17 +33,24 @@ def _ginibre_counts(n, N, seed, dtype=np.int32):
     return sc.sample_cdf(thr, N, seed=seed + 1, dtype=dtype)
 
 
+@pytest.mark.parametrize("path", ["tensor", "fwht"])
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("dtype", [np.int32, np.int16])
-def test_theta_bit_exact_and_rho(env, n, dtype):
+def test_theta_bit_exact_and_rho(env, n, dtype, path):
+    """Both first-pass paths (the tensor-core one applies to int16 counts with
+    n >= 6; every other case runs the FWHT kernels under either setting)."""
     torch, lre, ctx = env
     N = 1000
     counts = _ginibre_counts(n, N, seed=10 * n, dtype=dtype)
     c = torch.from_numpy(counts).cuda()
     theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
     rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda")
-    lre.lre_estimate(ctx, c, N, n, theta, rho)
-    lre.lre_sync(ctx)
+    lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if path == "tensor" else lre.LRE_FOLD_FWHT)
+    try:
+        lre.lre_estimate(ctx, c, N, n, theta, rho)
+        lre.lre_sync(ctx)
+    finally:
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
     t_ref = direct.estimate(counts, N, n)
     np.testing.assert_array_equal(theta.cpu().numpy(), t_ref)
     assert rel_fro(rho.cpu().numpy(), direct.mu(t_ref, n)) <= 1e-6

@@ -1,6 +1,9 @@
 """Tensor-core form of the first fold pass (tcgen05.mma kind::f16, exact
 small integers, FP32 accumulation in TMEM): bit-identical to the FWHT path
-and to the oracle."""
+and to the oracle, for both operand encodings (raw counts read as fp16 bit
+patterns, and fp16(1024 + c))."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -17,12 +20,73 @@ def _counts(torch, n, shots, seed, dt=np.int16):
     return c
 
 
+def _set_variant(lre, ctx, biased):
+    f = lre.load().lre_debug_set_mma_variant
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_int
+    assert f(ctx, biased) == 0
+
+
+@pytest.mark.parametrize("biased", [0, 1])
 @pytest.mark.parametrize("n", [7, 8, 10, 11])
-def test_tensor_parity_sums_equal_fwht(n):
+def test_tensor_parity_sums_equal_fwht(n, biased):
     torch = need_gpu()
     lre, ctx = ctx_and_lre()
     try:
+        _set_variant(lre, ctx, biased)
         c = _counts(torch, n, 1000, 90 + n)
+        res = []
+        for path in (lre.LRE_FOLD_FWHT, lre.LRE_FOLD_TENSOR):
+            lre.lre_set_fold_path(ctx, path)
+            S = torch.empty(4 ** n, dtype=torch.int64, device="cuda")
+            lre.lre_profile(ctx, True)
+            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=1000)
+            lre.lre_sync(ctx)
+            names = [k for k, _ in lre.lre_profile_records(ctx)]
+            lre.lre_profile(ctx, False)
+            assert ("fold_first6_mma" in names) == (path == lre.LRE_FOLD_TENSOR), names
+            res.append(S)
+        assert torch.equal(res[0], res[1])
+    finally:
+        lre.lre_destroy(ctx)
+
+
+@pytest.mark.parametrize("biased,top", [(0, 2047), (1, 1023)])
+def test_tensor_theta_matches_oracle_at_largest_counts(biased, top):
+    """Counts up to the largest value each encoding keeps exact; one count
+    above it sends the call down the FWHT path, still exact."""
+    torch = need_gpu()
+    lre, ctx = ctx_and_lre()
+    try:
+        _set_variant(lre, ctx, biased)
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+        n = 8
+        rng = np.random.default_rng(3 + biased)
+        p = np.r_[0.9, np.full(2 ** n - 1, 0.1 / (2 ** n - 1))]
+        raw = rng.multinomial(top, p, size=3 ** n)
+        raw[::7, 0] = top  # full-weight rows: every count in one outcome
+        raw[::7, 1:] = 0
+        raw = raw.astype(np.int16)
+        theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+        lre.lre_estimate(ctx, torch.from_numpy(raw).cuda(), top, n, theta)
+        lre.lre_sync(ctx)
+        np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(raw, top, n))
+        raw2 = rng.multinomial(top + 1, np.ones(2 ** n) / 2 ** n, size=3 ** n).astype(np.int16)
+        lre.lre_estimate(ctx, torch.from_numpy(raw2).cuda(), top + 1, n, theta)
+        lre.lre_sync(ctx)
+        np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(raw2, top + 1, n))
+    finally:
+        lre.lre_destroy(ctx)
+
+
+def test_tensor_first_pass_n12_equals_fwht():
+    """Headline-shaped case: many tiles per CTA, both level-B warp pairs and
+    every ring slot in use."""
+    torch = need_gpu()
+    lre, ctx = ctx_and_lre()
+    try:
+        n = 12
+        c = _counts(torch, n, 1000, 1234)
         res = []
         for path in (lre.LRE_FOLD_FWHT, lre.LRE_FOLD_TENSOR):
             lre.lre_set_fold_path(ctx, path)
@@ -31,28 +95,6 @@ def test_tensor_parity_sums_equal_fwht(n):
             lre.lre_sync(ctx)
             res.append(S)
         assert torch.equal(res[0], res[1])
-    finally:
-        lre.lre_destroy(ctx)
-
-
-def test_tensor_theta_matches_oracle_and_worst_case_counts():
-    torch = need_gpu()
-    lre, ctx = ctx_and_lre()
-    try:
-        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
-        n = 7
-        rng = np.random.default_rng(3)
-        # worst case for the fp16 bias trick: counts up to 1023 (1023 shots)
-        raw = rng.multinomial(1023, np.r_[0.9, np.full(2 ** n - 1, 0.1 / (2 ** n - 1))], size=3 ** n)
-        raw = raw.astype(np.int16)
-        theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
-        lre.lre_estimate(ctx, torch.from_numpy(raw).cuda(), 1023, n, theta)
-        lre.lre_sync(ctx)
-        np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(raw, 1023, n))
-        # 1024 shots and int32 counts take the FWHT path and stay exact
-        raw2 = rng.multinomial(1024, np.ones(2 ** n) / 2 ** n, size=3 ** n).astype(np.int16)
-        lre.lre_estimate(ctx, torch.from_numpy(raw2).cuda(), 1024, n, theta)
-        lre.lre_sync(ctx)
-        np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(raw2, 1024, n))
+        assert int(res[1][0]) == 1000 * 3 ** n
     finally:
         lre.lre_destroy(ctx)
