@@ -266,18 +266,25 @@ def run_e2e(args, wl, lre, torch, device, theta_dev):
     for _ in range(args.warmup):
         lre.lre_estimate_host(ctx, host_in, kind, N, n, theta_h, rho_h, stream=stream)
     torch.cuda.synchronize()
+    per_step = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        lre.lre_estimate_host(ctx, host_in, kind, N, n, theta_h, rho_h, stream=stream)
+        t1 = time.perf_counter()
+        lre.lre_estimate_host(ctx, host_in, kind, N, n, theta_h, rho_h, stream=stream)  # returns synchronised
+        per_step.append(time.perf_counter() - t1)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
     same = bool(torch.equal(theta_h, theta_dev.cpu())) if theta_dev is not None else None
     lre.lre_destroy(ctx)
+    per_step.sort()
     return {"value": round(B / dt, 1), "unit": "Pauli bases/s", "seconds_per_step": round(dt, 4),
+            "step_seconds_median_min_max": [round(per_step[len(per_step) // 2], 4), round(per_step[0], 4),
+                                            round(per_step[-1], 4)],
             "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
             "d2h_bytes_per_step": theta_h.numel() * 8 + rho_h.numel() * 8,
-            "input": f"pinned host {what}; lre_estimate_host (chunked H2D on a copy stream, "
-                     f"device ingest, fold, assembly, D2H theta+rho)",
+            "input": f"pinned host {what}; lre_estimate_host (chunked H2D on a copy stream overlapped "
+                     f"with the device ingest and first fold pass per chunk, remaining passes, theta D2H "
+                     f"during the assembly, rho D2H)",
             "theta_equals_device_path": same}
 
 

@@ -172,10 +172,14 @@ lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_base
  * histograms on the device); shots_uniform: shots per basis (> 0);
  * theta_host: host FP64 [4^n]; rho_host: host complex64 [2^n][2^n] or NULL.
  * The input is copied in row chunks on a copy stream owned by the context,
- * overlapped with the ingest; the device work runs on `stream`; the call
- * returns when theta (and rho) are in host memory, with any latched kernel
- * error.  Device memory used: the counts (3^n 2^n x 2 or 4 bytes), theta, rho
- * and the fold workspace, all held in the context's workspace. */
+ * each copy overlapped with the device work on the chunk before it: the
+ * ingest and, for n >= 7, the six-qubit first fold pass over the chunk's
+ * whole tile rows (729 bases).  The other passes run after the last chunk;
+ * theta is copied back on the copy stream while rho is assembled on
+ * `stream`.  The call returns when theta (and rho) are in host memory, with
+ * any latched kernel error.  Device memory used: the counts (3^n 2^n x 2 or
+ * 4 bytes), theta, rho and the fold workspace, all held in the context's
+ * workspace. */
 lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind host_kind,
                              int64_t shots_uniform, int n, double *theta_host, lre_c64 *rho_host,
                              lre_stream stream);

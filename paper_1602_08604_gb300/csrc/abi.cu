@@ -85,6 +85,43 @@ __global__ void histogram_kernel(const uint16_t *__restrict__ rec, int64_t B, in
   }
 }
 
+// int16 counts (shots per basis <= 32767, so no bin carries into its
+// neighbour): two bins per 32-bit word of shared memory, so a basis of n = 14
+// takes 32 KB and seven CTAs fit an SM; zeroing and the store to HBM move 16
+// bytes (eight bins) per thread, and VEC reads eight records per load.
+template <bool VEC>
+__global__ void __launch_bounds__(256) histogram16_kernel(const uint16_t *__restrict__ rec, int64_t B, int64_t S,
+                                                         int n, int16_t *__restrict__ counts, int *status) {
+  extern __shared__ uint4 h4[];
+  uint32_t *h = reinterpret_cast<uint32_t *>(h4);
+  const int d = 1 << n, nv = d >> 3;
+  for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) h4[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const uint16_t *r = rec + b * S;
+    bool bad = false;
+    auto add = [&](uint32_t o) {
+      if (o < (uint32_t)d) atomicAdd(&h[o >> 1], 1u << ((o & 1u) << 4));
+      else bad = true;
+    };
+    if constexpr (VEC) {
+      const uint4 *r4 = reinterpret_cast<const uint4 *>(r);
+      for (int64_t v = threadIdx.x; v < (S >> 3); v += blockDim.x) {
+        const uint4 q = __ldcs(r4 + v);
+        add(q.x & 0xFFFFu); add(q.x >> 16); add(q.y & 0xFFFFu); add(q.y >> 16);
+        add(q.z & 0xFFFFu); add(q.z >> 16); add(q.w & 0xFFFFu); add(q.w >> 16);
+      }
+    } else {
+      for (int64_t t = threadIdx.x; t < S; t += blockDim.x) add(r[t]);
+    }
+    if (bad) latch(status, LRE_ERR_INVALID_ARG);
+    __syncthreads();
+    uint4 *c = reinterpret_cast<uint4 *>(counts + b * (int64_t)d);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) c[i] = h4[i];
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 lre_status histogram_run(lre_ctx *ctx, const uint16_t *records, int64_t num_bases,
@@ -94,7 +131,16 @@ lre_status histogram_run(lre_ctx *ctx, const uint16_t *records, int64_t num_base
   int grid = ctx->num_sms * 4;
   if (grid > num_bases) grid = (int)num_bases;
   Launch L(ctx, "histogram", s);
-  if (kind == LRE_COUNTS_I16) {
+  if (kind == LRE_COUNTS_I16 && n >= 3 && (reinterpret_cast<uintptr_t>(counts) & 15) == 0) {
+    const size_t smem16 = sizeof(int16_t) << n;
+    int grid16 = ctx->num_sms * 8;
+    if (grid16 > num_bases) grid16 = (int)num_bases;
+    const bool vec = (shots_per_basis & 7) == 0 && (reinterpret_cast<uintptr_t>(records) & 15) == 0;
+    auto k = vec ? histogram16_kernel<true> : histogram16_kernel<false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
+    k<<<grid16, 256, smem16, s>>>(records, num_bases, shots_per_basis, n, static_cast<int16_t *>(counts),
+                                  ctx->d_status);
+  } else if (kind == LRE_COUNTS_I16) {
     cudaFuncSetAttribute(histogram_kernel<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     histogram_kernel<int16_t><<<grid, 512, smem, s>>>(records, num_bases, shots_per_basis, n,
                                                       static_cast<int16_t *>(counts), ctx->d_status);
@@ -174,6 +220,7 @@ void lre_destroy(lre_ctx *ctx) {
     if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);
     if (ctx->ev_free[k]) cudaEventDestroy(ctx->ev_free[k]);
   }
+  if (ctx->ev_theta) cudaEventDestroy(ctx->ev_theta);
   for (auto &e : ctx->prof_pool) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);
@@ -344,6 +391,15 @@ uint64_t lre_launch_count(lre_ctx *ctx) { return ctx ? ctx->launches : 0; }
 extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   if (!ctx || variant < 0 || variant > 2) return LRE_ERR_INVALID_ARG;
   ctx->first_variant = variant;
+  return LRE_OK;
+}
+
+// Test hook (not part of include/lre.h): bytes of host input per streamed
+// chunk of lre_estimate_host (rounded to whole tile rows where the first pass
+// runs per chunk); small values exercise many chunks on small inputs.
+extern "C" lre_status lre_debug_set_host_chunk(lre_ctx *ctx, int64_t bytes) {
+  if (!ctx || bytes <= 0) return LRE_ERR_INVALID_ARG;
+  ctx->host_chunk_bytes = (size_t)bytes;
   return LRE_OK;
 }
 

@@ -645,6 +645,24 @@ __global__ void inv_shots_kernel(const int64_t *shots, double *w, int64_t B, int
   }
 }
 
+namespace {
+
+bool tensor_first_pass(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
+  return pp.first6 && !pp.fused9 && ctx->fold_path == 1 && ctx->mma_operand && pp.in_t == T_I16 &&
+         a.shots == nullptr && a.shots_uniform > 0 && a.shots_uniform <= mma_max_count(ctx->mma_biased);
+}
+
+}  // namespace
+
+int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a) {
+  if (a.shots) return 0;
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(a.counts) & 15) == 0;
+  auto plan = make_plan(a.n, a.kind, false, a.S != nullptr, a.shots_uniform, aligned16, ctx->first_variant);
+  if (plan.empty() || !plan[0].first6 || plan[0].fused9) return 0;
+  // the tensor-core and TMA-pipeline kernels take tile ranges; the register kernel does not
+  return (tensor_first_pass(ctx, plan[0], a) || ctx->first_variant >= 1) ? 729 : 0;
+}
+
 lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
   const bool weighted = a.shots != nullptr;
   const bool parity = a.S != nullptr;
@@ -669,32 +687,45 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
     inv_shots_kernel<<<256, 256, 0, s>>>(a.shots, wgt, B, ctx->d_status);
   }
   const void *in = a.counts;
-  for (size_t k = 0; k < plan.size(); ++k) {
+  size_t k_begin = 0, k_end = plan.size();
+  if (a.stage != 0) {
+    if (fold_split_rows(ctx, a) == 0) return LRE_ERR_UNSUPPORTED;
+    if (a.stage == 1) {
+      k_end = 1;
+    } else {
+      k_begin = 1;
+      in = bufA;  // the first pass's output
+    }
+  }
+  for (size_t k = k_begin; k < k_end; ++k) {
     const PassPlan &pp = plan[k];
+    const int64_t all_tiles = pp.first6 ? (ipow(3, pp.r - 6) << (pp.r - 6)) : 0;
+    const int64_t tile_begin = a.stage == 1 ? a.ah_begin << (pp.r - 6) : 0;
+    const int64_t tile_end = a.stage == 1 ? a.ah_end << (pp.r - 6) : all_tiles;
+    if (a.stage == 1 && (tile_begin < 0 || tile_end > all_tiles || tile_end < tile_begin)) return LRE_ERR_INVALID_ARG;
+    if (a.stage == 1 && tile_end == tile_begin) return LRE_OK;
     void *out;
     if (pp.mode == M_STORE)
       out = (k % 2 == 0) ? bufA : bufB;
     else
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
     CUtensorMap tmap, tmap_tail;
-    const bool tensor = pp.first6 && !pp.fused9 && ctx->fold_path == 1 && ctx->mma_operand &&
-                        pp.in_t == T_I16 && a.shots_uniform > 0 &&
-                        a.shots_uniform <= mma_max_count(ctx->mma_biased);
+    const bool tensor = tensor_first_pass(ctx, pp, a);
     if (tensor && make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(0)) &&
         make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
       lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), pp.r,
-                                     ctx->mma_biased, s);
+                                     ctx->mma_biased, tile_begin, tile_end, s);
       if (st != LRE_OK) return st;
     } else if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
         make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {
-      const int64_t tiles = ipow(3, pp.r - 6) << (pp.r - 6);
+      const int64_t tiles = tile_end - tile_begin;
       int grid = ctx->num_sms;
       if ((int64_t)grid > tiles) grid = (int)tiles;
       PipeArgs A{};
       A.out = static_cast<int32_t *>(out);
       A.n = pp.r;
-      A.tile_begin = 0;
-      A.tile_end = tiles;
+      A.tile_begin = tile_begin;
+      A.tile_end = tile_end;
       A.row_base = 0;
       A.status = ctx->d_status;
       A.fuse = pp.fused9 ? 1 : 0;

@@ -84,7 +84,8 @@ __device__ __forceinline__ int32_t d_to_int(uint32_t bits, float scale, int32_t 
 template <bool BIASED>
 __global__ void __launch_bounds__(MMA_THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
-                    const uint4 *__restrict__ gA, int32_t *__restrict__ out, int n, int64_t tiles, int *status) {
+                    const uint4 *__restrict__ gA, int32_t *__restrict__ out, int n, int64_t tile_begin,
+                    int64_t tile_end, int *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *Am = smem;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     *abort_flag = 1;
     latch(status, LRE_ERR_TIMEOUT);
   };
+  const int64_t tiles = tile_end - tile_begin;
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int64_t total = my_tiles * 2;  // chunks of this CTA
 
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     if (lane == 0) {
       int64_t g = 0;
       for (; g < total && !*abort_flag; ++g) {
-        const int64_t tile = blockIdx.x + (g >> 1) * gridDim.x;
+        const int64_t tile = tile_begin + blockIdx.x + (g >> 1) * gridDim.x;
         const int c = (int)(g & 1);
         const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
         const int slot = (int)(g % MMA_R);
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
       }
       sm103::tc_fence_before();
       sm103::mbar_arrive(&tile_free[pair]);
-      const int64_t tile = blockIdx.x + lt * gridDim.x;
+      const int64_t tile = tile_begin + blockIdx.x + lt * gridDim.x;
       int32_t *o = out + tile * 4096 + plA;
 #pragma unroll
       for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
@@ -296,19 +298,21 @@ size_t mma_operand_bytes() { return A_BYTES; }
 uint32_t mma_box_rows(int which) { return which ? BOX_TAIL : BOX_BIG; }
 int64_t mma_max_count(int biased) { return biased ? 1023 : 2047; }
 
-// Launch the tensor-core first pass over all tiles of an n-qubit int16 count
-// matrix.  map_big / map_tail are tensor maps of the counts with boxes of
-// 216 / 81 rows x 64 outcomes; a_dev holds the operand written by
-// mma_operand_upload; every count must be at most mma_max_count(biased).
+// Launch the tensor-core first pass over tiles [tile_begin, tile_end) of an
+// n-qubit int16 count matrix (tile = ah * 2^(n-6) + oh).  map_big / map_tail
+// are tensor maps of the counts with boxes of 216 / 81 rows x 64 outcomes;
+// a_dev holds the operand written by mma_operand_upload; every count must be
+// at most mma_max_count(biased).
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
-                          int32_t *out, int n, int biased, cudaStream_t s) {
-  const int64_t tiles = ipow(3, n - 6) << (n - 6);
+                          int32_t *out, int n, int biased, int64_t tile_begin, int64_t tile_end, cudaStream_t s) {
+  const int64_t tiles = tile_end - tile_begin;
+  if (tiles <= 0) return LRE_OK;
   const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
   Launch L(ctx, "fold_first6_mma", s);
   auto kern = biased ? fold_first6_mma<true> : fold_first6_mma<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
-  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, n, tiles,
-                                           ctx->d_status);
+  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, n,
+                                           tile_begin, tile_end, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }

@@ -2,11 +2,14 @@
 //
 // The input (dense counts or per-basis shot records) is streamed to the
 // device in row chunks on a copy stream owned by the context, each chunk's
-// copy overlapping the ingest of the previous one (records are histogrammed
-// into device counts by the ingest kernel).  The device path then runs
-// exactly as lre_estimate, and theta / rho are copied back.  Host buffers
-// should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to run
-// asynchronously; pageable memory works but serialises.
+// copy overlapping the device work on the previous one: records are
+// histogrammed into device counts, and where the fold plan starts with the
+// six-qubit first pass (n >= 7, uniform shots) that pass runs on each chunk's
+// whole tile rows (729 basis rows each) as soon as they are counted.  The
+// remaining passes follow; theta is copied back on the copy stream while the
+// assembly of rho runs, and rho last.  Host buffers should be pinned
+// (cudaHostAlloc / cudaHostRegister) for the copies to run asynchronously;
+// pageable memory works but serialises.
 #include <cuda_runtime.h>
 
 #include "lre_internal.cuh"
@@ -29,9 +32,15 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
   const size_t counts_bytes = (size_t)B * d * csz;
   const size_t theta_bytes = (size_t)ipow(4, n) * sizeof(double);
   const size_t rho_bytes = rho_host ? (size_t)d * d * sizeof(lre_c64) : 0;
-  // chunk: a whole number of rows, about 256 MB of host input
+  // the device buffers come first (the first-pass split depends on the
+  // counts' alignment); chunk: a whole number of rows, about 256 MB of host
+  // input, and a whole number of tile rows when the first pass runs per chunk
   const size_t row_in = records ? (size_t)shots * sizeof(uint16_t) : (size_t)d * csz;
-  int64_t rows = (int64_t)((256ull << 20) / row_in);
+  FoldArgs probe{nullptr, ck, n, nullptr, shots, nullptr, nullptr};
+  probe.counts = reinterpret_cast<const void *>((uintptr_t)256);  // 256-byte aligned, as in the workspace
+  const int64_t unit = fold_split_rows(ctx, probe);
+  int64_t rows = (int64_t)(ctx->host_chunk_bytes / row_in);
+  if (unit > 0) rows = (rows / unit > 0 ? rows / unit : 1) * unit;
   if (rows < 1) rows = 1;
   if (rows > B) rows = B;
   const size_t chunk_in = (size_t)rows * row_in;
@@ -59,8 +68,12 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
       e = cudaEventCreateWithFlags(&ctx->ev_copied[k], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_free[k], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_theta, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
   }
+  FoldArgs fa{counts, ck, n, nullptr, shots, theta, nullptr};
+  fa.T = T;
+  const bool split = unit > 0 && fold_split_rows(ctx, fa) == unit;
   cudaStream_t cs = ctx->copy_stream;
   // the copy stream must not run ahead of work the caller queued on s
   e = cudaEventRecord(ctx->ev_free[0], s);
@@ -81,15 +94,27 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
       if (st != LRE_OK) return st;
     }
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_free[slot], s);
+    if (e == cudaSuccess && split) {  // first pass over this chunk's tile rows
+      FoldArgs f1 = fa;
+      f1.stage = 1;
+      f1.ah_begin = r0 / unit;
+      f1.ah_end = (r0 + nr) / unit;
+      if ((st = fold_run(ctx, f1, ws, dev_ws, s)) != LRE_OK) return st;
+    }
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host input streaming");
-  FoldArgs fa{counts, ck, n, nullptr, shots, theta, nullptr};
-  fa.T = T;
-  if ((st = fold_run(ctx, fa, ws, dev_ws, s)) != LRE_OK) return st;
+  FoldArgs rest = fa;
+  rest.stage = split ? 2 : 0;
+  if ((st = fold_run(ctx, rest, ws, dev_ws, s)) != LRE_OK) return st;
+  // theta is final: copy it back on the copy stream while rho is assembled
+  e = cudaEventRecord(ctx->ev_theta, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->ev_theta, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(theta_host, theta, theta_bytes, cudaMemcpyDeviceToHost, cs);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "theta copy-back");
   if (rho_host && (st = assemble_int_run(ctx, T, n, shots, rho, ws, s)) != LRE_OK) return st;
-  e = cudaMemcpyAsync(theta_host, theta, theta_bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && rho_host) e = cudaMemcpyAsync(rho_host, rho, rho_bytes, cudaMemcpyDeviceToHost, s);
+  if (rho_host) e = cudaMemcpyAsync(rho_host, rho, rho_bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host outputs");
   int code = 0;
   e = cudaMemcpy(&code, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);

@@ -42,9 +42,11 @@ struct lre_ctx {
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
   std::vector<char> batch_host;  // host copy of the last batched pass table
+  size_t host_chunk_bytes = 256ull << 20; // host-input streaming: bytes of input per chunk
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  cudaEvent_t ev_theta = nullptr;         // theta final: its copy-back may start
 };
 
 namespace lre {
@@ -86,10 +88,18 @@ struct FoldArgs {
   double *theta;          // final FP64 output (estimate mode) or nullptr
   int64_t *S;             // final int64 output (parity-sum mode) or nullptr
   int64_t *T = nullptr;   // optional exact integers S_i 3^(n-k_i) (uniform shots)
+  // Split execution for streamed input: stage 0 runs every pass; stage 1 only
+  // the six-qubit first pass over basis rows [ah_begin, ah_end) * 729; stage 2
+  // every pass after it (the first pass's output already in the workspace).
+  int stage = 0;
+  int64_t ah_begin = 0, ah_end = -1;
 };
 size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound,
                             int variant = 2);
 lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s);
+// Basis rows per unit of the stage-1 split (729), or 0 when these arguments
+// cannot be split (no six-qubit first pass, or one without tile ranges).
+int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a);
 
 // ---- step (ii): theta -> rho -------------------------------------------------
 size_t assemble_workspace_bytes(int n);
@@ -117,7 +127,7 @@ uint32_t mma_box_rows(int which);    // TMA box rows: 0 the 216-row box, 1 the 8
 int64_t mma_max_count(int biased);   // largest count the operand encoding keeps exact
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
-                          int32_t *out, int n, int biased, cudaStream_t s);
+                          int32_t *out, int n, int biased, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
 
 // ---- batched instances (one persistent launch) ---------------------------------
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);

@@ -229,10 +229,24 @@ __device__ __forceinline__ longlong2 load_first(const long long *in, int64_t i) 
   return mk(__ldcg(in + i), 0ll);
 }
 
-// int64 -> float of v * (sh + sl), error about half an ulp of the float
+// int64 -> float of v * (sh + sl), error about half an ulp of the float.
+// 64-bit integer conversions run at the FP64 rate, so v is split as
+// a 2^46 + b 2^23 + c with 0 <= b, c < 2^23 and |a| < 2^17; each part becomes
+// a float exactly by placing it in the mantissa of 2^23 (or 1.5 * 2^23 for
+// the signed a) and subtracting that constant.  X = a 2^46 + b 2^23 is exact
+// while |v| < 2^46 (a is 0 or -1) and rounded once above; Knuth's TwoSum then
+// gives vh = RN(X + c) and the exact remainder vl, and the product with the
+// two-float scale is formed with one final rounding.
 __device__ __forceinline__ float scaled(long long v, const LastScale &s) {
-  const float vh = (float)v;
-  const float vl = (float)(v - (long long)vh);
+  const int a = (int)(v >> 46);
+  const unsigned b = (unsigned)(v >> 23) & 0x7FFFFFu, c = (unsigned)v & 0x7FFFFFu;
+  const float fa = __int_as_float(0x4B400000 + a) - 12582912.f;
+  const float fb = __int_as_float(0x4B000000 | b) - 8388608.f;
+  const float fc = __int_as_float(0x4B000000 | c) - 8388608.f;
+  const float X = __fmaf_rn(fa, 70368744177664.f, fb * 8388608.f);  // 2^46, 2^23
+  const float vh = __fadd_rn(X, fc);
+  const float bv = __fsub_rn(vh, X);
+  const float vl = __fadd_rn(__fsub_rn(X, __fsub_rn(vh, bv)), __fsub_rn(fc, bv));
   return __fmaf_rn(vh, s.sh, __fmaf_rn(vh, s.sl, vl * s.sh));
 }
 __device__ __forceinline__ float2 to_c64(double2 v, const LastScale &) {

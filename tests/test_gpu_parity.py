@@ -128,17 +128,36 @@ def test_projection_of_physical_state_is_identity(env):
     np.testing.assert_array_equal(out.cpu().numpy(), mu.cpu().numpy())
 
 
-def test_histogram_ingest(env):
+@pytest.mark.parametrize("n,B,S", [(5, 243, 777), (5, 243, 800), (2, 9, 40), (10, 300, 4096),
+                                   (14, 40, 32760)])
+def test_histogram_ingest(env, n, B, S):
+    """Scalar and eight-records-per-load paths (S a multiple of 8 or not),
+    the generic kernel below n = 3, packed 16-bit bins up to 32760 shots in
+    one bin."""
     torch, lre, ctx = env
-    n, B, S = 5, 243, 777
-    rng = np.random.default_rng(8)
-    rec = rng.integers(0, 2 ** n, size=(B, S)).astype(np.int16)
-    want = np.stack([np.bincount(r, minlength=2 ** n) for r in rec])
+    rng = np.random.default_rng(8 + n)
+    rec = rng.integers(0, 2 ** n, size=(B, S)).astype(np.uint16)
+    rec[0, :] = 2 ** n - 1      # every shot in one bin (odd index: the high half of a word)
+    rec[1, :] = 0               # and in bin 0
+    want = np.stack([np.bincount(r, minlength=2 ** n) for r in rec.astype(np.int64)])
+    dev = torch.from_numpy(rec.view(np.int16)).cuda()
     for dt in (torch.int32, torch.int16):
-        out = torch.empty((B, 2 ** n), dtype=dt, device="cuda")
-        lre.lre_histogram(ctx, torch.from_numpy(rec).cuda(), n, out)
+        out = torch.full((B, 2 ** n), -3, dtype=dt, device="cuda")
+        lre.lre_histogram(ctx, dev, n, out)
         lre.lre_sync(ctx)
         np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_histogram_rejects_out_of_range_record(env):
+    torch, lre, ctx = env
+    n = 6
+    rec = np.zeros((27, 64), dtype=np.uint16)
+    rec[5, 7] = 2 ** n
+    out = torch.empty((27, 2 ** n), dtype=torch.int16, device="cuda")
+    lre.lre_histogram(ctx, torch.from_numpy(rec.view(np.int16)).cuda(), n, out)
+    with pytest.raises(lre.LreError) as e:
+        lre.lre_sync(ctx)
+    assert e.value.status == lre.LRE_ERR_INVALID_ARG
 
 
 def test_device_generators_match_cpu(env):
@@ -187,11 +206,21 @@ def test_errors_and_latched_status(env):
         lre.lre_destroy(ctx2)
 
 
-@pytest.mark.parametrize("n,kind", [(6, "records"), (7, "i16"), (8, "i32"), (3, "records")])
-def test_estimate_host_matches_device_path(env, n, kind):
+@pytest.mark.parametrize("n,kind,chunk", [(6, "records", 0), (7, "i16", 0), (8, "i32", 0), (3, "records", 0),
+                                         (9, "records", 1), (9, "i16", 1500000), (10, "records", 3000000),
+                                         (8, "i32", 1)])
+def test_estimate_host_matches_device_path(env, n, kind, chunk):
     """End to end from pinned host memory (records histogrammed on device)
-    gives the same bits as the device path and the oracle."""
+    gives the same bits as the device path and the oracle; chunk > 0 forces
+    small streamed chunks (rounded up to one tile row of 729 bases), so the
+    first fold pass runs on many chunks."""
     torch, lre, ctx = env
+    import ctypes
+    L = lre.load()
+    f = L.lre_debug_set_host_chunk
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    f.restype = ctypes.c_int
+    assert f(ctx, chunk if chunk else 256 << 20) == 0
     from synth import gen
     N = 1000
     if kind == "records":
@@ -210,7 +239,10 @@ def test_estimate_host_matches_device_path(env, n, kind):
         hk = lre.LRE_HOST_COUNTS_I16 if kind == "i16" else lre.LRE_HOST_COUNTS_I32
     th = torch.empty(4 ** n, dtype=torch.float64).pin_memory()
     rh = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64).pin_memory()
-    lre.lre_estimate_host(ctx, host_in, hk, N, n, th, rh)
+    try:
+        lre.lre_estimate_host(ctx, host_in, hk, N, n, th, rh)
+    finally:
+        assert f(ctx, 256 << 20) == 0
     t_ref = direct.estimate(counts, N, n)
     np.testing.assert_array_equal(th.numpy(), t_ref)
     assert rel_fro(rh.numpy(), direct.mu(t_ref, n)) <= 1e-6
