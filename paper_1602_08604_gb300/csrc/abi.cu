@@ -394,6 +394,15 @@ extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   return LRE_OK;
 }
 
+// Test hook (not part of include/lre.h): fold passes after the first read
+// their inputs through TMA boxes in shared memory (1, the default, where the
+// pass allows) or with per-thread global loads (0).
+extern "C" lre_status lre_debug_set_generic_tma(lre_ctx *ctx, int on) {
+  if (!ctx || on < 0 || on > 1) return LRE_ERR_INVALID_ARG;
+  ctx->generic_tma = on;
+  return LRE_OK;
+}
+
 // Test hook (not part of include/lre.h): bytes of host input per streamed
 // chunk of lre_estimate_host (rounded to whole tile rows where the first pass
 // runs per chunk); small values exercise many chunks on small inputs.

@@ -620,6 +620,24 @@ size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+bool encode_tensor_map_i32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                           const uint64_t *strides, const uint32_t *box) {
+  EncodeTiled enc = encode_fn();
+  if (!enc || rank < 1 || rank > 5) return false;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) st[i] = strides[i];
+  }
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT32, rank, const_cast<void *>(base), d, st, bx, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 constexpr size_t FUSE_SCRATCH_BYTES = (size_t)FUSE_RING * 216 * 4096 * 4;
 
 size_t fuse_bytes(const std::vector<PassPlan> &plan) {
@@ -785,11 +803,17 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
         gp.up3[k] = k <= a.n ? ipow(3, a.n - k) : 0;
       }
       gp.status = ctx->d_status;
-      int64_t blocks = (gp.items + 255) / 256;
-      const int64_t cap = (int64_t)ctx->num_sms * 64;
-      if (blocks > cap) blocks = cap;
-      Launch L(ctx, pp.mode == M_STORE ? "fold_pass" : "fold_final", s);
-      kern<<<(unsigned)blocks, 256, 0, s>>>(gp);
+      lre_status tst = ctx->generic_tma ? tma_pass(ctx, gp, pp.J, pp.in_t, pp.acc_t, pp.mode, pp.weight, s)
+                                        : LRE_ERR_UNSUPPORTED;
+      if (tst == LRE_ERR_UNSUPPORTED) {
+        int64_t blocks = (gp.items + 255) / 256;
+        const int64_t cap = (int64_t)ctx->num_sms * 64;
+        if (blocks > cap) blocks = cap;
+        Launch L(ctx, pp.mode == M_STORE ? "fold_pass" : "fold_final", s);
+        kern<<<(unsigned)blocks, 256, 0, s>>>(gp);
+      } else if (tst != LRE_OK) {
+        return tst;
+      }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fold pass launch");

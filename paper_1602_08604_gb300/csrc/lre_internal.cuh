@@ -39,6 +39,7 @@ struct lre_ctx {
   int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores where the input allows
   void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
   int mma_biased = 0;         // tensor-core operand: 0 raw counts as fp16 bits, 1 fp16(1024 + c)
+  int generic_tma = 1;        // later fold passes: 1 TMA-staged kernel where it applies, 0 register loads
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
   std::vector<char> batch_host;  // host copy of the last batched pass table
@@ -100,6 +101,11 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
 // Basis rows per unit of the stage-1 split (729), or 0 when these arguments
 // cannot be split (no six-qubit first pass, or one without tile ranges).
 int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a);
+
+// Tiled TMA descriptor of an int32 tensor (dims and box innermost first,
+// strides in bytes of dims 1..rank-1); false if the driver rejects it.
+bool encode_tensor_map_i32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                           const uint64_t *strides, const uint32_t *box);
 
 // ---- step (ii): theta -> rho -------------------------------------------------
 size_t assemble_workspace_bytes(int n);

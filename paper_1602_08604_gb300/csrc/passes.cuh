@@ -124,6 +124,40 @@ __device__ __forceinline__ void ld_row_vec(const InT *p, V (&v)[NO]) {
   }
 }
 
+// Writes the NP outputs of one column (ahoh, c) of a fold pass: partial sums
+// (M_STORE), exact parity sums (M_PARITY), or theta = S / (N 3^k) (uniform
+// shots, with the exact T_i = S_i 3^(n-k) when requested) / the weighted sum
+// / 3^k (M_FINAL_W).
+template <int J, typename AccT, int MODE>
+__device__ __forceinline__ void fold_emit(const GenParams &P, const AccT (&acc)[1 << (2 * J)], int64_t ahoh,
+                                          int64_t c) {
+  constexpr int NP = 1 << (2 * J);
+  const int64_t obase = ahoh * NP * P.C + c;
+  if constexpr (MODE == M_STORE) {
+    AccT *out = static_cast<AccT *>(P.out);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = acc[p];
+  } else if constexpr (MODE == M_PARITY) {
+    int64_t *out = static_cast<int64_t *>(P.out);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = (int64_t)acc[p];
+  } else {
+    double *out = static_cast<double *>(P.out);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int64_t i = obase + p * P.C;  // ahoh == 0 in the last pass
+      const int k = identity_letters((uint64_t)i, P.n);
+      if constexpr (MODE == M_FINAL_U) {
+        if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
+        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
+        if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
+      } else {
+        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
+      }
+    }
+  }
+}
+
 // One output column (ah, oh, c) of a fold pass.  VEC: first pass (C == 1),
 // the row's 2^J outcomes loaded as one vector.
 template <int J, typename InT, typename AccT, int MODE, bool WEIGHT, bool COHERENT = false, bool VEC = false>
@@ -164,31 +198,13 @@ __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
     }
   }
-  const int64_t obase = ahoh * NP * P.C + c;
-  if constexpr (MODE == M_STORE) {
-    AccT *out = static_cast<AccT *>(P.out);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = acc[p];
-  } else if constexpr (MODE == M_PARITY) {
-    int64_t *out = static_cast<int64_t *>(P.out);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = (int64_t)acc[p];
-  } else {
-    double *out = static_cast<double *>(P.out);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const int64_t i = obase + p * P.C;  // ahoh == 0 in the last pass
-      const int k = identity_letters((uint64_t)i, P.n);
-      if constexpr (MODE == M_FINAL_U) {
-        if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
-        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
-        if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
-      } else {
-        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
-      }
-    }
-  }
+  fold_emit<J, AccT, MODE>(P, acc, ahoh, c);
 }
+
+// TMA-staged generic fold pass (fold_tma.cu) for int32 inputs with C a
+// multiple of 32; LRE_ERR_UNSUPPORTED (nothing launched) for other passes.
+lre_status tma_pass(lre_ctx *ctx, const GenParams &P, int J, int in_t, int acc_t, int mode, bool weight,
+                    cudaStream_t s);
 
 // ---- step (ii) ----------------------------------------------------------------
 struct NumF64 {
