@@ -394,6 +394,15 @@ extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   return LRE_OK;
 }
 
+// Test hook (not part of include/lre.h): step (iii) through the
+// eigenvalue-first path (1, the default, for d >= 64) or always through the
+// full eigendecomposition (0).
+extern "C" lre_status lre_debug_set_project_mode(lre_ctx *ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 1) return LRE_ERR_INVALID_ARG;
+  ctx->project_mode = mode;
+  return LRE_OK;
+}
+
 // Test hook (not part of include/lre.h): fold passes after the first read
 // their inputs through TMA boxes in shared memory (1, the default, where the
 // pass allows) or with per-thread global loads (0).

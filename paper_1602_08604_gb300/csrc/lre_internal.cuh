@@ -39,6 +39,7 @@ struct lre_ctx {
   int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores where the input allows
   void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
   int mma_biased = 0;         // tensor-core operand: 0 raw counts as fp16 bits, 1 fp16(1024 + c)
+  int project_mode = 1;       // step (iii): 1 eigenvalue-first where it applies, 0 full eigendecomposition
   int generic_tma = 1;        // later fold passes: 1 TMA-staged kernel where it applies, 0 register loads
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
@@ -122,6 +123,17 @@ LastScaleArgs int_assembly_scale(int n, int64_t shots);
 // ---- step (iii): rho -> physical rho ----------------------------------------
 lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,
                        double *eig_mu, double *eig_rho, cudaStream_t s);
+
+// tridiagonal eigenproblem kernels (tridiag.cu)
+constexpr int TRI_THREADS = 256;
+__global__ void tri_bisect_kernel(const double *a, const double *b2, int64_t n, double lo0, double hi0, double tol,
+                                  double pivmin, double *W);
+constexpr int TRI_ROUNDS = 3;  // inverse-iteration rounds
+__global__ void tri_factor(const double *a, const double *b, int64_t n, const double *lam, int m, double tnorm,
+                           double *lu);
+__global__ void tri_solve(const double *lu, int64_t n, int m, double *X, int first);
+__global__ void tri_orthonormalise(double *X, int64_t n, const int *cl);
+__global__ void tri_clusters(const double *lam, int m, double gap_tol, int *cl, int *k_out);
 
 // ---- end to end from host memory ---------------------------------------------
 lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, int64_t shots,
