@@ -528,6 +528,13 @@ def run_batched(args):
     ms_batch = timed(lambda: lre.lre_batch_run(ctx, items, stream=stream))
     batch_launches = (lre.lre_launch_count(ctx) - launches0) // (args.steps + args.warmup)
     theta_b = [it[3].clone() for it in items]
+    # the same launch captured once in a CUDA graph and replayed
+    side = torch.cuda.Stream(device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        lre.lre_batch_run(ctx, items, stream=torch.cuda.current_stream(device))
+    ms_graph = timed(graph.replay)
+    same_graph = all(torch.equal(a, it[3]) for a, it in zip(theta_b, items))
     launches0 = lre.lre_launch_count(ctx)
     ms_single = timed(lambda: [lre.lre_estimate(ctx, c, s, n, t, r, stream=stream) for c, s, n, t, r in items])
     single_launches = (lre.lre_launch_count(ctx) - launches0) // (args.steps + args.warmup)
@@ -546,6 +553,7 @@ def run_batched(args):
         "batched": {"ms": round(ms_batch, 4), "launches_per_step": batch_launches,
                     "count_gbs": round(count_bytes / (ms_batch / 1e3) / 1e9, 1),
                     "frac_hbm_counts": round(count_bytes / (ms_batch / 1e3) / 1e9 / peak, 4)},
+        "graph_replay": {"ms": round(ms_graph, 4), "theta_equal": same_graph},
         "one_launch_per_instance": {"ms": round(ms_single, 4), "launches_per_step": single_launches},
         "speedup_vs_per_instance": round(ms_single / ms_batch, 2),
         "theta_equal_batched_vs_single": same, "gpu_launches": batch_launches * args.steps,

@@ -193,7 +193,16 @@ lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind ho
  * lists of all instances are cut into 256-item work units that the CTAs of
  * one grid claim in pass-major order; a unit waits (bounded by time, then
  * LRE_ERR_TIMEOUT is latched) for its instance's previous pass.  n > 9 in
- * any instance returns LRE_ERR_UNSUPPORTED (use lre_estimate). */
+ * any instance returns LRE_ERR_UNSUPPORTED (use lre_estimate).
+ * CUDA graphs: the call may be captured (cudaStreamBeginCapture or any
+ * wrapper of it) once the same batch -- the same descriptors -- has run
+ * uncaptured on this context; that run sizes the workspace and stores the
+ * batch's pass table in a device buffer the context keeps until
+ * lre_destroy, and the captured launch reuses both (a capture without such a
+ * run returns LRE_ERR_UNSUPPORTED and enqueues nothing).  A replay reads the
+ * buffers the descriptors point to at replay time, and uses the context's
+ * workspace: replays and other calls on the same context must not overlap,
+ * and a later call that grows the workspace invalidates earlier graphs. */
 lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream);
 
 /* Autotuner for lre_batch_run: times the candidate schedules (qubits per

@@ -215,6 +215,7 @@ void lre_destroy(lre_ctx *ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->mma_operand) cudaFree(ctx->mma_operand);
+  for (auto &en : ctx->batch_cache) cudaFree(en.table);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (int k = 0; k < 2; ++k) {
     if (ctx->ev_copied[k]) cudaEventDestroy(ctx->ev_copied[k]);

@@ -307,11 +307,18 @@ lre_status validate(const lre_instance *inst, int count) {
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s) {
   lre_status st = validate(inst, count);
   if (st != LRE_OK) return st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "capture status");
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
   const int jmax = ctx->batch_jmax;
   // layout: [BatchState][done counters][phase table][instance workspaces]
   Plan probe = build_plan(inst, count, jmax, nullptr);
   const size_t nph = probe.phases.size();
   const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) + up256(nph * sizeof(BPhase));
+  if (capturing && ctx->ws_bytes < head + probe.ws_bytes) {
+    ctx->last_error = "lre_batch_run under stream capture: run the same batch once uncaptured first";
+    return LRE_ERR_UNSUPPORTED;
+  }
   if ((st = ensure_workspace(ctx, head + probe.ws_bytes)) != LRE_OK) return st;
   char *w = static_cast<char *>(ctx->ws);
   BatchState *bs = reinterpret_cast<BatchState *>(w);
@@ -319,26 +326,58 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   BPhase *dph = reinterpret_cast<BPhase *>(w + up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)));
   Plan plan = build_plan(inst, count, jmax, w + head);
   for (auto &b : plan.phases) b.g.status = ctx->d_status;
-  ctx->batch_host.resize(nph * sizeof(BPhase));
-  std::copy(reinterpret_cast<const char *>(plan.phases.data()),
-            reinterpret_cast<const char *>(plan.phases.data()) + nph * sizeof(BPhase), ctx->batch_host.data());
-  cudaError_t e = cudaMemsetAsync(w, 0, up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)), s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dph, ctx->batch_host.data(), nph * sizeof(BPhase), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch plan upload");
-  int per_sm = 0;
-  if (jmax >= 3)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<3>, 256, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<2>, 256, 0);
-  per_sm = std::max(1, std::min(per_sm, ctx->batch_ctas_per_sm));
+  // The pass table lives in a device buffer per distinct table (kept until
+  // lre_destroy), so a captured launch reads a table no later call rewrites;
+  // under capture the table must already exist (no allocation, no host copy).
+  const char *bytes = reinterpret_cast<const char *>(plan.phases.data());
+  const size_t tbytes = nph * sizeof(BPhase);
+  const BPhase *table = nullptr;
+  for (const auto &en : ctx->batch_cache)
+    if (en.ws == ctx->ws && en.key.size() == tbytes && std::equal(en.key.begin(), en.key.end(), bytes)) {
+      table = static_cast<const BPhase *>(en.table);
+      break;
+    }
+  cudaError_t e = cudaSuccess;
+  if (!table) {
+    if (capturing) {
+      ctx->last_error = "lre_batch_run under stream capture: run the same batch once uncaptured first";
+      return LRE_ERR_UNSUPPORTED;
+    }
+    constexpr size_t kMaxTables = 64;
+    void *t = nullptr;
+    if (ctx->batch_cache.size() < kMaxTables && cudaMalloc(&t, tbytes) == cudaSuccess) {
+      lre_batch_entry en;
+      en.key.assign(bytes, bytes + tbytes);
+      en.table = t;
+      en.ws = ctx->ws;
+      ctx->batch_cache.push_back(std::move(en));
+      // pageable source: staged before the call returns
+      e = cudaMemcpyAsync(t, ctx->batch_cache.back().key.data(), tbytes, cudaMemcpyHostToDevice, s);
+      table = static_cast<const BPhase *>(t);
+    } else {
+      cudaGetLastError();
+      e = cudaMemcpyAsync(dph, bytes, tbytes, cudaMemcpyHostToDevice, s);
+      table = dph;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch plan upload");
+  }
+  e = cudaMemsetAsync(w, 0, up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch state reset");
+  int &occ = ctx->batch_occupancy[jmax >= 3 ? 1 : 0];  // queried once, outside any capture
+  if (occ == 0) {
+    if (jmax >= 3)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<3>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<2>, 256, 0);
+  }
+  const int per_sm = std::max(1, std::min(occ, ctx->batch_ctas_per_sm));
   const int grid = ctx->num_sms * per_sm;  // every CTA resident: waits always resolve
   {
     Launch L(ctx, "batch_kernel", s);
     if (jmax >= 3)
-      batch_kernel<3><<<grid, 256, 0, s>>>(dph, (int)nph, done, bs, plan.total_units, ctx->d_status);
+      batch_kernel<3><<<grid, 256, 0, s>>>(table, (int)nph, done, bs, plan.total_units, ctx->d_status);
     else
-      batch_kernel<2><<<grid, 256, 0, s>>>(dph, (int)nph, done, bs, plan.total_units, ctx->d_status);
+      batch_kernel<2><<<grid, 256, 0, s>>>(table, (int)nph, done, bs, plan.total_units, ctx->d_status);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "batch kernel launch");

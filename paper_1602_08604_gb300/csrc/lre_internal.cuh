@@ -18,6 +18,15 @@ struct lre_prof_entry {
   cudaEvent_t start, stop;
 };
 
+// One batched pass table kept on the device (lre_batch_run): the table's
+// bytes, its device copy, and the workspace it points into.  Entries are
+// immutable, so a CUDA graph that captured a launch over one stays valid.
+struct lre_batch_entry {
+  std::vector<char> key;
+  void *table = nullptr;
+  void *ws = nullptr;
+};
+
 struct lre_ctx {
   int device = 0;
   int num_sms = 0;
@@ -43,7 +52,8 @@ struct lre_ctx {
   int generic_tma = 1;        // later fold passes: 1 TMA-staged kernel where it applies, 0 register loads
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
-  std::vector<char> batch_host;  // host copy of the last batched pass table
+  int batch_occupancy[2] = {0, 0};  // most resident CTAs per SM of batch_kernel<2>, <3>
+  std::vector<lre_batch_entry> batch_cache;  // device pass tables of earlier batched calls
   size_t host_chunk_bytes = 256ull << 20; // host-input streaming: bytes of input per chunk
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};

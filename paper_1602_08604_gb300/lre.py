@@ -209,7 +209,7 @@ def lre_batch_tune(ctx, items, stream=None):
 
 
 def lre_set_fold_path(ctx, path):
-    """LRE_FOLD_FWHT (default) or LRE_FOLD_TENSOR (tcgen05 first pass)."""
+    """LRE_FOLD_TENSOR (default; tcgen05 first pass where it applies) or LRE_FOLD_FWHT."""
     _check(load().lre_set_fold_path(ctx, int(path)), ctx)
 
 

@@ -86,3 +86,52 @@ def test_batch_rejects_large_n(batch):
         assert e.value.status == lre.LRE_ERR_UNSUPPORTED
     finally:
         lre.lre_destroy(ctx)
+
+
+def test_batch_captured_in_a_cuda_graph_replays_on_new_counts(batch):
+    """The batched launch recorded in a CUDA graph: replaying it after the
+    counts change in place gives exactly the per-instance results on the new
+    counts."""
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    try:
+        small = [it for it in items if it[2] <= 7]
+        lre.lre_batch_run(ctx, small)          # uncaptured run: workspace and pass table
+        lre.lre_sync(ctx)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            lre.lre_batch_run(ctx, small, stream=torch.cuda.current_stream())
+        rng = np.random.default_rng(5)
+        new_host = []
+        for (c, shots, n, theta, rho) in small:
+            fresh = _instance(n, int(rng.integers(1000, 2000)), shots,
+                              np.int16 if c.dtype == torch.int16 else np.int32)
+            c.copy_(torch.from_numpy(fresh))
+            theta.zero_()
+            new_host.append((fresh, shots, n))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        lre.lre_sync(ctx)
+        _check_against_single(torch, lre, ctx, small, new_host)
+    finally:
+        lre.lre_destroy(ctx)
+
+
+def test_batch_capture_without_uncaptured_run_is_refused(batch):
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    try:
+        small = [it for it in items if it[2] <= 5]
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        err = None
+        with torch.cuda.graph(g, stream=s):
+            try:
+                lre.lre_batch_run(ctx, small, stream=torch.cuda.current_stream())
+            except lre.LreError as ex:
+                err = ex
+        assert err is not None and err.status == lre.LRE_ERR_UNSUPPORTED
+    finally:
+        lre.lre_destroy(ctx)
