@@ -32,6 +32,7 @@ using namespace passes;
 // pass bodies a unit can run
 enum : int {
   C_FOLD = 0,    // + (J-1)*8 + first*4 + (in_i16 ? 0 : 2) + (final ? 1 : 0): J in 1..3 -> 0..23
+                 //   (no final pass of three qubits: codes 17, 19, 21, 23 are never planned)
   C_ASM = 32,    // + (J-1)*4 + first*2 + last: J in 1..2 -> 32..39
 };
 
@@ -72,26 +73,14 @@ __device__ __forceinline__ void run_item(const BPhase &P, int64_t item) {
     case C_FOLD + 16:
       if constexpr (JMAX >= 3) fold_item<3, int16_t, int32_t, M_STORE, false, true, false>(P.g, item);
       break;
-    case C_FOLD + 17:
-      if constexpr (JMAX >= 3) fold_item<3, int16_t, int64_t, M_FINAL_U, false, true, false>(P.g, item);
-      break;
     case C_FOLD + 18:
       if constexpr (JMAX >= 3) fold_item<3, int32_t, int32_t, M_STORE, false, true, false>(P.g, item);
-      break;
-    case C_FOLD + 19:
-      if constexpr (JMAX >= 3) fold_item<3, int32_t, int64_t, M_FINAL_U, false, true, false>(P.g, item);
       break;
     case C_FOLD + 20:
       if constexpr (JMAX >= 3) fold_item<3, int16_t, int32_t, M_STORE, false, false, true>(P.g, item);
       break;
-    case C_FOLD + 21:
-      if constexpr (JMAX >= 3) fold_item<3, int16_t, int64_t, M_FINAL_U, false, false, true>(P.g, item);
-      break;
     case C_FOLD + 22:
       if constexpr (JMAX >= 3) fold_item<3, int32_t, int32_t, M_STORE, false, false, true>(P.g, item);
-      break;
-    case C_FOLD + 23:
-      if constexpr (JMAX >= 3) fold_item<3, int32_t, int64_t, M_FINAL_U, false, false, true>(P.g, item);
       break;
     case C_ASM + 0: asm_item<NumI64, 1, false, false>(P.a, item); break;
     case C_ASM + 1: asm_item<NumI64, 1, false, true>(P.a, item); break;
@@ -105,32 +94,47 @@ __device__ __forceinline__ void run_item(const BPhase &P, int64_t item) {
   }
 }
 
+constexpr int BATCH_SMEM_PHASES = 4096;  // phase starts cached in shared memory up to this many
+
+// Last phase with unit_begin <= u (binary search over the phase starts).
+__device__ __forceinline__ int find_phase(const int64_t *begin, int nph, int64_t u) {
+  int lo = 0, hi = nph - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <int JMAX>
-__global__ void __launch_bounds__(256) batch_kernel(const BPhase *__restrict__ ph, int nph,
-                                                   unsigned *__restrict__ done, BatchState *st,
+__global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict__ ph, const int64_t *__restrict__ gbegin,
+                                                   int nph, unsigned *__restrict__ done, BatchState *st,
                                                    int64_t total_units, int *status) {
+  extern __shared__ int64_t sbegin[];  // phase starts (when nph <= BATCH_SMEM_PHASES)
   __shared__ int64_t s_unit;
   __shared__ int s_phase, s_ok;
   volatile int *abort = &st->abort;
+  const bool cached = nph <= BATCH_SMEM_PHASES;
+  if (cached)
+    for (int k = threadIdx.x; k < nph; k += blockDim.x) sbegin[k] = gbegin[k];
+  __syncthreads();
+  const int64_t *begin = cached ? sbegin : gbegin;
+  unsigned long long u = 0;
+  if (threadIdx.x == 0) u = atomicAdd(&st->next_unit, 1ull);
   for (;;) {
     if (threadIdx.x == 0) {
-      const unsigned long long u = atomicAdd(&st->next_unit, 1ull);
       int p = -1, ok = 1;
       if ((int64_t)u < total_units && !*abort) {
-        int lo = 0, hi = nph - 1;  // last phase with unit_begin <= u
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (ph[mid].unit_begin <= (int64_t)u) lo = mid;
-          else hi = mid - 1;
-        }
-        p = lo;
+        p = find_phase(begin, nph, (int64_t)u);
         const int dep = ph[p].dep;
         if (dep >= 0) {
+          const unsigned need = ph[p].dep_units;
           const uint64_t t0 = sm103::globaltimer();
           for (uint32_t it = 0;; ++it) {
             unsigned v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(done + dep) : "memory");
-            if (v >= ph[p].dep_units) break;
+            if (v >= need) break;
             if ((it & 63u) == 63u) {
               if (*abort || sm103::globaltimer() - t0 > sm103::kWaitNs) {
                 ok = 0;
@@ -155,6 +159,11 @@ __global__ void __launch_bounds__(256) batch_kernel(const BPhase *__restrict__ p
       }
       break;
     }
+    // claim the next unit now: the atomic's round trip overlaps this unit's
+    // work.  Every wait still points at a smaller unit than the waiter's own
+    // (dependencies are earlier phases, a CTA's next unit is larger than its
+    // current one), so the smallest unfinished unit always runs.
+    if (threadIdx.x == 0) u = atomicAdd(&st->next_unit, 1ull);
     const BPhase &P = ph[p];
     const int64_t item = (s_unit - P.unit_begin) * 256 + threadIdx.x;
     if (item < P.items) run_item<JMAX>(P, item);
@@ -193,7 +202,11 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
     };
     std::vector<P0> fp;
     while (r > 0) {
-      const int J = std::min(r, jmax);
+      // the final pass contracts at most two qubits: its int64 sums and FP64
+      // quotients for three would need about 180 registers per thread, which
+      // would leave one CTA per SM for every pass of the launch
+      int J = std::min(r, jmax);
+      if (r == 3 && J == 3) J = 2;
       fp.push_back({J, r, C, in16, J == r});
       const size_t ob = fp.back().last ? 0 : (size_t)ipow(6, r - J) * (size_t)ipow(4, J) * C * 4;
       if (fp.size() % 2) bufA = std::max(bufA, ob);
@@ -314,7 +327,8 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   // layout: [BatchState][done counters][phase table][instance workspaces]
   Plan probe = build_plan(inst, count, jmax, nullptr);
   const size_t nph = probe.phases.size();
-  const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) + up256(nph * sizeof(BPhase));
+  const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) +
+                      up256(nph * (sizeof(BPhase) + sizeof(int64_t)));
   if (capturing && ctx->ws_bytes < head + probe.ws_bytes) {
     ctx->last_error = "lre_batch_run under stream capture: run the same batch once uncaptured first";
     return LRE_ERR_UNSUPPORTED;
@@ -326,11 +340,17 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   BPhase *dph = reinterpret_cast<BPhase *>(w + up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)));
   Plan plan = build_plan(inst, count, jmax, w + head);
   for (auto &b : plan.phases) b.g.status = ctx->d_status;
-  // The pass table lives in a device buffer per distinct table (kept until
-  // lre_destroy), so a captured launch reads a table no later call rewrites;
-  // under capture the table must already exist (no allocation, no host copy).
-  const char *bytes = reinterpret_cast<const char *>(plan.phases.data());
-  const size_t tbytes = nph * sizeof(BPhase);
+  // The pass table (phases, then their first units) lives in a device buffer
+  // per distinct table (kept until lre_destroy), so a captured launch reads a
+  // table no later call rewrites; under capture the table must already exist
+  // (no allocation, no host copy).
+  std::vector<char> tab(nph * (sizeof(BPhase) + sizeof(int64_t)));
+  std::copy(reinterpret_cast<const char *>(plan.phases.data()),
+            reinterpret_cast<const char *>(plan.phases.data()) + nph * sizeof(BPhase), tab.data());
+  for (size_t k = 0; k < nph; ++k)
+    reinterpret_cast<int64_t *>(tab.data() + nph * sizeof(BPhase))[k] = plan.phases[k].unit_begin;
+  const char *bytes = tab.data();
+  const size_t tbytes = tab.size();
   const BPhase *table = nullptr;
   for (const auto &en : ctx->batch_cache)
     if (en.ws == ctx->ws && en.key.size() == tbytes && std::equal(en.key.begin(), en.key.end(), bytes)) {
@@ -365,19 +385,26 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch state reset");
   int &occ = ctx->batch_occupancy[jmax >= 3 ? 1 : 0];  // queried once, outside any capture
   if (occ == 0) {
-    if (jmax >= 3)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<3>, 256, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<2>, 256, 0);
+    // with the largest phase-start cache: every CTA of the grid must be resident
+    const size_t sm_max = BATCH_SMEM_PHASES * sizeof(int64_t);
+    if (jmax >= 3) {
+      cudaFuncSetAttribute(batch_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_max);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<3>, 256, sm_max);
+    } else {
+      cudaFuncSetAttribute(batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_max);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<2>, 256, sm_max);
+    }
   }
   const int per_sm = std::max(1, std::min(occ, ctx->batch_ctas_per_sm));
   const int grid = ctx->num_sms * per_sm;  // every CTA resident: waits always resolve
+  const int64_t *starts = reinterpret_cast<const int64_t *>(table + nph);
+  const size_t smem = nph <= (size_t)BATCH_SMEM_PHASES ? nph * sizeof(int64_t) : 0;
   {
     Launch L(ctx, "batch_kernel", s);
     if (jmax >= 3)
-      batch_kernel<3><<<grid, 256, 0, s>>>(table, (int)nph, done, bs, plan.total_units, ctx->d_status);
+      batch_kernel<3><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, ctx->d_status);
     else
-      batch_kernel<2><<<grid, 256, 0, s>>>(table, (int)nph, done, bs, plan.total_units, ctx->d_status);
+      batch_kernel<2><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, ctx->d_status);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "batch kernel launch");
