@@ -39,32 +39,15 @@ __global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
     asm_item<Num, J, FIRST, LAST>(P, item);
 }
 
-template <typename V>
-__device__ __forceinline__ void m2(V (&v)[16]) {
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    V a, b, c, d;
-    m_qubit(v[4 * h + 0], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3], a, b, c, d);
-    v[4 * h + 0] = a; v[4 * h + 1] = b; v[4 * h + 2] = c; v[4 * h + 3] = d;
-  }
-#pragma unroll
-  for (int u0 = 0; u0 < 4; ++u0) {
-    V a, b, c, d;
-    m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
-    v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Shared-memory tiled passes (n >= 10): a 6-qubit first pass over contiguous
-// blocks of 4096 coefficients, then 4-qubit passes over 16-column strips.
-// Each thread holds 16 complex values (two qubits) per round; rounds
-// exchange through shared memory (one padding element per 16: at most 4
-// wavefronts per 16-byte warp access).
+// blocks of 4096 coefficients (asm_low6_block in passes.cuh, shared with the
+// batched kernel), then 4-qubit passes over 16-column strips.  Each thread
+// holds 16 complex values (two qubits) per round; rounds exchange through
+// shared memory (one padding element per 16: at most 4 wavefronts per
+// 16-byte warp access).
 // ---------------------------------------------------------------------------
-constexpr int TILE_SMEM = (4096 + 256) * 16;
-
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+constexpr int TILE_SMEM = ASM_TILE_SMEM;
 
 // First pass: qubits 0..5 of each block of 4096 coefficients ->
 // [R_lo 64][C_lo 64] per block.
@@ -74,39 +57,8 @@ __global__ void __launch_bounds__(256) assemble_low6(const typename Num::In *__r
   using V = typename Num::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *S = reinterpret_cast<V *>(smem_raw);  // 4096 + 256 padded entries
-  const int tid = threadIdx.x;
-  for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int i = tid + 256 * k;
-      S[pad16(i)] = load_first(in, blk * 4096 + i);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const int sh = 4 * r;
-      const int lo = tid & ((1 << sh) - 1), hi = tid >> sh;
-      V v[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = S[pad16(lo | (u << sh) | (hi << (sh + 4)))];
-      m2(v);
-#pragma unroll
-      for (int u = 0; u < 16; ++u) S[pad16(lo | (u << sh) | (hi << (sh + 4)))] = v[u];
-      __syncthreads();
-    }
-    // S[pos], pos digit q = 2 r_q + c_q  ->  out[R_lo * 64 + C_lo]
-    V *dst = out + blk * 4096;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int o = tid + 256 * k;
-      const int R = o >> 6, C = o & 63;
-      int pos = 0;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) pos |= ((((R >> q) & 1) << 1) | ((C >> q) & 1)) << (2 * q);
-      dst[o] = S[pad16(pos)];
-    }
-    __syncthreads();
-  }
+  for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x)
+    asm_low6_block<Num, false>(in, out, blk, S, LastScale{0.f, 0.f});
 }
 
 // 4-qubit pass over qubits t..t+3 (t >= 6): unit = (P', R_lo, 16 consecutive

@@ -34,13 +34,14 @@ enum : int {
   C_FOLD = 0,    // + (J-1)*8 + first*4 + (in_i16 ? 0 : 2) + (final ? 1 : 0): J in 1..3 -> 0..23
                  //   (no final pass of three qubits: codes 17, 19, 21, 23 are never planned)
   C_ASM = 32,    // + (J-1)*4 + first*2 + last: J in 1..2 -> 32..39
+  C_ASM6 = 48,   // + last: the first six assembly qubits of one 4096-coefficient block per unit
 };
 
 struct BPhase {
   int code;
   int dep;          // index of the phase this one waits for (-1: none)
   unsigned dep_units;
-  int pad;
+  int per_unit;     // items per work unit: 256 (one per thread) or 1 (a shared-memory block)
   int64_t unit_begin, units, items;
   GenParams g;
   AsmParams a;
@@ -110,8 +111,11 @@ __device__ __forceinline__ int find_phase(const int64_t *begin, int nph, int64_t
 template <int JMAX>
 __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict__ ph, const int64_t *__restrict__ gbegin,
                                                    int nph, unsigned *__restrict__ done, BatchState *st,
-                                                   int64_t total_units, int *status) {
-  extern __shared__ int64_t sbegin[];  // phase starts (when nph <= BATCH_SMEM_PHASES)
+                                                   int64_t total_units, int tile_bytes, int *status) {
+  // dynamic shared memory: [assembly tile (tile_bytes)][phase starts]
+  extern __shared__ __align__(16) unsigned char bsmem[];
+  int64_t *sbegin = reinterpret_cast<int64_t *>(bsmem + tile_bytes);
+  NumI64::V *tile = reinterpret_cast<NumI64::V *>(bsmem);
   __shared__ int64_t s_unit;
   __shared__ int s_phase, s_ok;
   volatile int *abort = &st->abort;
@@ -165,8 +169,17 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict_
     // current one), so the smallest unfinished unit always runs.
     if (threadIdx.x == 0) u = atomicAdd(&st->next_unit, 1ull);
     const BPhase &P = ph[p];
-    const int64_t item = (s_unit - P.unit_begin) * 256 + threadIdx.x;
-    if (item < P.items) run_item<JMAX>(P, item);
+    if (P.code >= C_ASM6) {  // uniform across the CTA: every thread takes part in the block
+      const int64_t blk = s_unit - P.unit_begin;
+      const auto *in = static_cast<const long long *>(P.a.in);
+      if (P.code == C_ASM6 + 1)
+        asm_low6_block<NumI64, true>(in, P.a.out, blk, tile, P.a.scale);
+      else
+        asm_low6_block<NumI64, false>(in, P.a.out, blk, tile, P.a.scale);
+    } else {
+      const int64_t item = (s_unit - P.unit_begin) * 256 + threadIdx.x;
+      if (item < P.items) run_item<JMAX>(P, item);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(done + p, 1u);
@@ -252,6 +265,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
         g.up3[kk] = kk <= n ? ipow(3, n - kk) : 0;
       }
       b.items = g.items;
+      b.per_unit = 256;
       per[i].push_back(b);
       in = g.out;
     }
@@ -259,6 +273,25 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
       const LastScaleArgs sc = int_assembly_scale(n, I.shots);
       int tt = 0, kk = 0;
       const void *ain = T;
+      if (n >= 6) {
+        // the first six qubits of each 4096-coefficient block in shared memory
+        const bool last = n == 6;
+        BPhase b{};
+        b.code = C_ASM6 + (last ? 1 : 0);
+        AsmParams &a = b.a;
+        a.in = ain;
+        a.out = last ? static_cast<void *>(I.rho) : static_cast<void *>(ab[0]);
+        a.t = 0;
+        a.n = n;
+        a.items = 1ll << (2 * (n - 6));  // blocks
+        a.scale = LastScale{sc.sh, sc.sl};
+        b.items = a.items;
+        b.per_unit = 1;
+        per[i].push_back(b);
+        ain = a.out;
+        tt = 6;
+        kk = 1;
+      }
       while (tt < n) {
         const int J = (n - tt) >= 2 ? 2 : 1;
         const bool first = tt == 0, last = tt + J == n;
@@ -272,6 +305,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
         a.items = (1ll << (2 * (n - tt - J))) << (2 * tt);
         a.scale = LastScale{sc.sh, sc.sl};
         b.items = a.items;
+        b.per_unit = 256;
         per[i].push_back(b);
         ain = a.out;
         tt += J;
@@ -289,7 +323,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
     for (int i = 0; i < count; ++i) {
       if (k >= per[i].size()) continue;
       BPhase b = per[i][k];
-      b.units = (b.items + 255) / 256;
+      b.units = (b.items + b.per_unit - 1) / b.per_unit;
       b.unit_begin = u;
       u += b.units;
       b.dep = last_index[i];
@@ -386,7 +420,7 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   int &occ = ctx->batch_occupancy[jmax >= 3 ? 1 : 0];  // queried once, outside any capture
   if (occ == 0) {
     // with the largest phase-start cache: every CTA of the grid must be resident
-    const size_t sm_max = BATCH_SMEM_PHASES * sizeof(int64_t);
+    const size_t sm_max = ASM_TILE_SMEM + BATCH_SMEM_PHASES * sizeof(int64_t);
     if (jmax >= 3) {
       cudaFuncSetAttribute(batch_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_max);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<3>, 256, sm_max);
@@ -398,13 +432,18 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   const int per_sm = std::max(1, std::min(occ, ctx->batch_ctas_per_sm));
   const int grid = ctx->num_sms * per_sm;  // every CTA resident: waits always resolve
   const int64_t *starts = reinterpret_cast<const int64_t *>(table + nph);
-  const size_t smem = nph <= (size_t)BATCH_SMEM_PHASES ? nph * sizeof(int64_t) : 0;
+  bool any_block = false;
+  for (const auto &b : plan.phases) any_block = any_block || b.code >= C_ASM6;
+  const int tile_bytes = any_block ? ASM_TILE_SMEM : 0;
+  const size_t smem = tile_bytes + (nph <= (size_t)BATCH_SMEM_PHASES ? nph * sizeof(int64_t) : 0);
   {
     Launch L(ctx, "batch_kernel", s);
     if (jmax >= 3)
-      batch_kernel<3><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, ctx->d_status);
+      batch_kernel<3><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, tile_bytes,
+                                              ctx->d_status);
     else
-      batch_kernel<2><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, ctx->d_status);
+      batch_kernel<2><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, tile_bytes,
+                                              ctx->d_status);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "batch kernel launch");

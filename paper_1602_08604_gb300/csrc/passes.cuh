@@ -340,5 +340,71 @@ __device__ __forceinline__ void asm_item(const AsmParams &P, int64_t item) {
   }
 }
 
+// ---- shared-memory tile of the assembly's first six qubits ---------------------
+constexpr int ASM_TILE_SMEM = (4096 + 256) * 16;
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// The per-qubit map on two qubits of 16 values (index u = d0 + 4 d1).
+template <typename V>
+__device__ __forceinline__ void m2(V (&v)[16]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    V a, b, c, d;
+    m_qubit(v[4 * h + 0], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3], a, b, c, d);
+    v[4 * h + 0] = a; v[4 * h + 1] = b; v[4 * h + 2] = c; v[4 * h + 3] = d;
+  }
+#pragma unroll
+  for (int u0 = 0; u0 < 4; ++u0) {
+    V a, b, c, d;
+    m_qubit(v[u0], v[4 + u0], v[8 + u0], v[12 + u0], a, b, c, d);
+    v[u0] = a; v[4 + u0] = b; v[8 + u0] = c; v[12 + u0] = d;
+  }
+}
+
+// Qubits 0..5 of block `blk` (4096 consecutive coefficients of the first
+// pass's input) -> [R_lo 64][C_lo 64] at out + blk * 4096, through the padded
+// shared tile S (4096 + 256 entries).  All 256 threads of the CTA call it
+// together.  LAST: the block is the whole matrix (n = 6) and is written as
+// complex64 with the final scale.
+template <class Num, bool LAST>
+__device__ __forceinline__ void asm_low6_block(const typename Num::In *__restrict__ in, void *__restrict__ out,
+                                               int64_t blk, typename Num::V *S, const LastScale &scale) {
+  using V = typename Num::V;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int i = tid + 256 * k;
+    S[pad16(i)] = load_first(in, blk * 4096 + i);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int sh = 4 * r;
+    const int lo = tid & ((1 << sh) - 1), hi = tid >> sh;
+    V v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = S[pad16(lo | (u << sh) | (hi << (sh + 4)))];
+    m2(v);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) S[pad16(lo | (u << sh) | (hi << (sh + 4)))] = v[u];
+    __syncthreads();
+  }
+  // S[pos], pos digit q = 2 r_q + c_q  ->  out[R_lo * 64 + C_lo]
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int o = tid + 256 * k;
+    const int R = o >> 6, C = o & 63;
+    int pos = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) pos |= ((((R >> q) & 1) << 1) | ((C >> q) & 1)) << (2 * q);
+    if constexpr (LAST)
+      static_cast<float2 *>(out)[blk * 4096 + o] = to_c64(S[pad16(pos)], scale);
+    else
+      static_cast<V *>(out)[blk * 4096 + o] = S[pad16(pos)];
+  }
+  __syncthreads();
+}
+
 }  // namespace passes
 }  // namespace lre
