@@ -262,6 +262,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
         const double p3 = (double)ipow(3, kk <= n ? kk : 0);
         g.denom[kk] = (double)I.shots * p3;
         g.recip[kk] = 1.0 / g.denom[kk];
+        g.dint[kk] = I.shots * ipow(3, kk <= n ? kk : 0);
         g.up3[kk] = kk <= n ? ipow(3, n - kk) : 0;
       }
       b.items = g.items;

@@ -472,9 +472,14 @@ bool make_count_map(CUtensorMap *map, const void *base, lre_count_kind kind, int
 // Generic pass: one thread per (ah, oh, c) column, J <= 3 qubits in registers.
 template <int J, typename InT, typename AccT, int MODE, bool WEIGHT>
 __global__ void __launch_bounds__(256) fold_generic(GenParams P) {
+  __shared__ DivTables tab;  // uniform-shot final pass: divisor tables per k
+  if constexpr (MODE == M_FINAL_U) {
+    load_div_tables(P, tab);
+    __syncthreads();
+  }
   for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < P.items;
        item += (int64_t)gridDim.x * blockDim.x)
-    fold_item<J, InT, AccT, MODE, WEIGHT>(P, item);
+    fold_item<J, InT, AccT, MODE, WEIGHT>(P, item, MODE == M_FINAL_U ? &tab : nullptr);
 }
 
 using GenKernel = void (*)(GenParams);
@@ -800,6 +805,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
         const double p3 = (double)ipow(3, k <= a.n ? k : 0);
         gp.denom[k] = weighted ? p3 : (double)a.shots_uniform * p3;  // exact: < 2^53
         gp.recip[k] = 1.0 / gp.denom[k];                              // host IEEE division
+        gp.dint[k] = weighted ? 0 : a.shots_uniform * ipow(3, k <= a.n ? k : 0);
         gp.up3[k] = k <= a.n ? ipow(3, a.n - k) : 0;
       }
       gp.status = ctx->d_status;
@@ -823,6 +829,26 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
 }
 
 }  // namespace lre
+
+namespace lre {
+namespace {
+__global__ void debug_div_kernel(const int64_t *S, int64_t count, int64_t D, double y, double *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = passes::div_int_rn(S[i], D, y);
+}
+}  // namespace
+}  // namespace lre
+
+// Test hook (not part of include/lre.h): out[i] = the final pass's correctly
+// rounded S[i] / D (device arrays of `count`), for 0 < D < 2^53.
+extern "C" lre_status lre_debug_div(lre_ctx *ctx, const int64_t *S, int64_t count, int64_t D, double *out,
+                                    lre_stream stream) {
+  using namespace lre;
+  if (!ctx || !S || !out || count <= 0 || D <= 0 || D >= (1ll << 53)) return LRE_ERR_INVALID_ARG;
+  debug_div_kernel<<<256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(S, count, D, 1.0 / (double)D, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "debug division");
+}
 
 // Test hook (not part of include/lre.h): run only the 6-qubit first pass of
 // step (i) over all tiles, variant 0 = register-only kernel, 1 = TMA

@@ -25,8 +25,15 @@ namespace {
 
 using namespace passes;
 
-constexpr int TMA_WARPS = 4;
 constexpr int TC = 32;  // columns per task
+
+// warps per CTA: four for J = 3 (a 27 KB box each, two buffers: 221 KB), 16
+// for the smaller boxes of J <= 2, whose passes carry more arithmetic per byte
+// (the final division of every coefficient)
+template <int J>
+__host__ __device__ constexpr int tma_warps() {
+  return J == 3 ? 4 : 16;
+}
 
 template <int J>
 __host__ __device__ constexpr int box_bytes() {
@@ -34,7 +41,9 @@ __host__ __device__ constexpr int box_bytes() {
 }
 
 template <int J, typename AccT, int MODE>
-__global__ void __launch_bounds__(TMA_WARPS * 32, 1) fold_tma(const __grid_constant__ CUtensorMap map, GenParams P) {
+__global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_constant__ CUtensorMap map,
+                                                                    GenParams P) {
+  constexpr int TMA_WARPS = tma_warps<J>();
   constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
   constexpr int NO = 1 << J;
   constexpr int NP = 1 << (2 * J);
@@ -45,6 +54,8 @@ __global__ void __launch_bounds__(TMA_WARPS * 32, 1) fold_tma(const __grid_const
   uint8_t *buf = smem + warp * 2 * BOX;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TMA_WARPS * 2 * BOX) + warp * 2;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + TMA_WARPS * 2 * BOX + TMA_WARPS * 16);
+  __shared__ DivTables tab;
+  if constexpr (MODE == M_FINAL_U) load_div_tables(P, tab);
   if (threadIdx.x == 0) *abort_flag = 0;
   if (lane == 0) {
     sm103::mbar_init(&bar[0], 1);
@@ -93,7 +104,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32, 1) fold_tma(const __grid_const
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
     }
     const int64_t ahoh = task / cblocks, cb = task - ahoh * cblocks;
-    fold_emit<J, AccT, MODE>(P, acc, ahoh, cb * TC + lane);
+    fold_emit<J, AccT, MODE>(P, acc, ahoh, cb * TC + lane, MODE == M_FINAL_U ? &tab : nullptr);
   }
   // no TMA may still write into shared memory when the CTA exits
   if (lane == 0) {
@@ -110,6 +121,7 @@ __global__ void __launch_bounds__(TMA_WARPS * 32, 1) fold_tma(const __grid_const
 
 template <int J, typename AccT, int MODE>
 lre_status launch(lre_ctx *ctx, const CUtensorMap &map, const GenParams &P, cudaStream_t s) {
+  constexpr int TMA_WARPS = tma_warps<J>();
   constexpr int smem = TMA_WARPS * 2 * box_bytes<J>() + TMA_WARPS * 16 + 16 + 128;
   auto k = fold_tma<J, AccT, MODE>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -126,7 +138,9 @@ lre_status launch(lre_ctx *ctx, const CUtensorMap &map, const GenParams &P, cuda
 lre_status passes::tma_pass(lre_ctx *ctx, const GenParams &P, int J, int in_t, int acc_t, int mode, bool weight,
                             cudaStream_t s) {
   if (in_t != T_I32 || J < 1 || J > 3 || P.C % TC != 0 || weight) return LRE_ERR_UNSUPPORTED;
-  if (mode != M_STORE && mode != M_PARITY && mode != M_FINAL_U) return LRE_ERR_UNSUPPORTED;
+  // final passes (the correctly rounded division of every coefficient) are
+  // ALU-bound and run faster in the register-load kernel at full occupancy
+  if (mode != M_STORE && mode != M_PARITY) return LRE_ERR_UNSUPPORTED;
   if (acc_t != T_I32 && acc_t != T_I64) return LRE_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(P.in) & 15) != 0) return LRE_ERR_UNSUPPORTED;
   const int NA = J == 1 ? 3 : J == 2 ? 9 : 27, NO = 1 << J;

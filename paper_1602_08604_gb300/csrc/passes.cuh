@@ -66,6 +66,63 @@ __device__ __forceinline__ double div_by_recip(double a, double b, double y) {
   return fma(r, y, q);
 }
 
+// RN(S / d) for integers |S| < 2^53 and 0 < d < 2^53, with y = RN(1/d), using
+// one FP64 multiply and integer arithmetic (GB300's FP64 pipe is narrow; the
+// Markstein form above costs a conversion and three FP64 operations).
+//   1. The exponent e of the quotient (a/d in [2^e, 2^(e+1)), a = |S|) comes
+//      from the leading bits of a and d; with s = 53 - e the integer
+//      quotient Q = floor(a 2^s / d) lies in [2^53, 2^54).
+//   2. q0 = RN(a y) has relative error below 2^-52, so q0 2^s (an integer)
+//      is within 5 of Q; the exact remainder R = a 2^s - Q d (|R| < 2^56,
+//      so its low 64 bits suffice) corrects it to floor, 0 <= R < d.
+//   3. The mantissa is Q >> 1 rounded to nearest even from the guard bit
+//      Q & 1 and the sticky R != 0; the result is that mantissa times 2^e.
+// A quotient of |S| >= 2^53 (not exact as a double anyway) takes the FP64 form.
+// ld = the leading-bit position of d, dn = d << (63 - ld) (precomputed per divisor).
+__device__ __forceinline__ double div_int_rn(int64_t S, int64_t D, double y, int ld, uint64_t dn) {
+  if (S == 0) return 0.0;
+  const uint64_t a = S < 0 ? (uint64_t)(-S) : (uint64_t)S;
+  if (a >= (1ull << 53)) return div_by_recip((double)S, (double)D, y);
+  const uint64_t d = (uint64_t)D;
+  const int la = 63 - __clzll((long long)a);
+  const int e = la - ld - (((a << (63 - la)) < dn) ? 1 : 0);
+  const int s = 53 - e;  // in [1, 106]: a/d >= 2^-53 and <= 2^53
+  // a as a double, exactly (a < 2^53), built from its bits
+  const double ad = __longlong_as_double((long long)(((uint64_t)(1023 + la) << 52) |
+                                                     ((a << (52 - la)) & 0xFFFFFFFFFFFFFull)));
+  const uint64_t qb = (uint64_t)__double_as_longlong(ad * y);
+  const int sh = (int)((qb >> 52) & 0x7FF) - 1023 - e + 1;  // q0 2^s = mantissa << sh, sh in {0, 1, 2}
+  uint64_t Q = ((qb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (sh > 0 ? sh : 0);
+  if (sh < 0) Q >>= -sh;
+  // |R| < 6 d < 2^56, so R is the low 64 bits of a 2^s - Q d read as signed
+  int64_t R = (int64_t)((s < 64 ? a << s : 0ull) - Q * d);
+#pragma unroll 1
+  for (int it = 0; it < 16 && R < 0; ++it) {
+    --Q;
+    R += (int64_t)d;
+  }
+#pragma unroll 1
+  for (int it = 0; it < 16 && R >= (int64_t)d; ++it) {
+    ++Q;
+    R -= (int64_t)d;
+  }
+  uint64_t m = Q >> 1;
+  int ee = e;
+  if ((Q & 1) && (R != 0 || (m & 1))) {
+    if (++m == (1ull << 53)) {
+      m = 1ull << 52;
+      ++ee;
+    }
+  }
+  const uint64_t bits = ((uint64_t)(S < 0) << 63) | ((uint64_t)(ee + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double div_int_rn(int64_t S, int64_t D, double y) {
+  const int ld = 63 - __clzll(D);
+  return div_int_rn(S, D, y, ld, (uint64_t)D << (63 - ld));
+}
+
 struct GenParams {
   const void *in;
   void *out;
@@ -80,6 +137,7 @@ struct GenParams {
   int *status;
   int64_t *T;            // optional: exact integers S_i 3^(n-k) for the integer assembly
   double denom[16];      // N 3^k (uniform) or 3^k (weighted), exact
+  int64_t dint[16];      // N 3^k as an integer (uniform shots)
   double recip[16];      // correctly rounded 1 / denom[k]
   int64_t up3[16];       // 3^(n-k)
 };
@@ -124,13 +182,39 @@ __device__ __forceinline__ void ld_row_vec(const InT *p, V (&v)[NO]) {
   }
 }
 
+// Per-k divisor tables of a final pass in shared memory: the lanes of a warp
+// index them with different k, which the kernel-parameter space would serve
+// one distinct address at a time.
+struct DivTables {
+  double denom[16];
+  double recip[16];
+  int64_t dint[16];
+  int64_t up3[16];
+  uint64_t dn[16];  // dint normalised to bit 63
+  int ld[16];       // leading-bit position of dint
+};
+
+__device__ __forceinline__ void load_div_tables(const GenParams &P, DivTables &t) {
+  if (threadIdx.x < 16) {
+    const int k = threadIdx.x;
+    t.denom[k] = P.denom[k];
+    t.recip[k] = P.recip[k];
+    t.dint[k] = P.dint[k];
+    t.up3[k] = P.up3[k];
+    const int64_t d = P.dint[k] > 0 ? P.dint[k] : 1;
+    t.ld[k] = 63 - __clzll(d);
+    t.dn[k] = (uint64_t)d << (63 - t.ld[k]);
+  }
+}
+
 // Writes the NP outputs of one column (ahoh, c) of a fold pass: partial sums
 // (M_STORE), exact parity sums (M_PARITY), or theta = S / (N 3^k) (uniform
 // shots, with the exact T_i = S_i 3^(n-k) when requested) / the weighted sum
-// / 3^k (M_FINAL_W).
+// / 3^k (M_FINAL_W).  tab: the divisor tables in shared memory, or nullptr to
+// read them from P.
 template <int J, typename AccT, int MODE>
 __device__ __forceinline__ void fold_emit(const GenParams &P, const AccT (&acc)[1 << (2 * J)], int64_t ahoh,
-                                          int64_t c) {
+                                          int64_t c, const DivTables *tab = nullptr) {
   constexpr int NP = 1 << (2 * J);
   const int64_t obase = ahoh * NP * P.C + c;
   if constexpr (MODE == M_STORE) {
@@ -149,8 +233,19 @@ __device__ __forceinline__ void fold_emit(const GenParams &P, const AccT (&acc)[
       const int k = identity_letters((uint64_t)i, P.n);
       if constexpr (MODE == M_FINAL_U) {
         if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);
-        out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
-        if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
+        if (tab) {
+          // every third output takes the FP64 form, the rest the integer form:
+          // both are correctly rounded (identical results), and the split keeps
+          // the FP64 pipe and the integer ALUs busy at the same time
+          if (p % 3 == 0)
+            out[i] = div_by_recip((double)acc[p], tab->denom[k], tab->recip[k]);
+          else
+            out[i] = div_int_rn((int64_t)acc[p], tab->dint[k], tab->recip[k], tab->ld[k], tab->dn[k]);
+          if (P.T) P.T[i] = (int64_t)acc[p] * tab->up3[k];
+        } else {
+          out[i] = div_int_rn((int64_t)acc[p], P.dint[k], P.recip[k]);
+          if (P.T) P.T[i] = (int64_t)acc[p] * P.up3[k];
+        }
       } else {
         out[i] = div_by_recip((double)acc[p], P.denom[k], P.recip[k]);
       }
@@ -161,7 +256,7 @@ __device__ __forceinline__ void fold_emit(const GenParams &P, const AccT (&acc)[
 // One output column (ah, oh, c) of a fold pass.  VEC: first pass (C == 1),
 // the row's 2^J outcomes loaded as one vector.
 template <int J, typename InT, typename AccT, int MODE, bool WEIGHT, bool COHERENT = false, bool VEC = false>
-__device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
+__device__ __forceinline__ void fold_item(const GenParams &P, int64_t item, const DivTables *tab = nullptr) {
   constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
   constexpr int NO = 1 << J;
   constexpr int NP = 1 << (2 * J);
@@ -198,7 +293,7 @@ __device__ __forceinline__ void fold_item(const GenParams &P, int64_t item) {
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
     }
   }
-  fold_emit<J, AccT, MODE>(P, acc, ahoh, c);
+  fold_emit<J, AccT, MODE>(P, acc, ahoh, c, tab);
 }
 
 // TMA-staged generic fold pass (fold_tma.cu) for int32 inputs with C a
