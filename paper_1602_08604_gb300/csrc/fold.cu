@@ -627,6 +627,11 @@ size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool encode_tensor_map_i32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
                            const uint64_t *strides, const uint32_t *box) {
+  return encode_tensor_map(map, CU_TENSOR_MAP_DATA_TYPE_INT32, base, rank, dims, strides, box);
+}
+
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, const void *base, int rank,
+                       const uint64_t *dims, const uint64_t *strides, const uint32_t *box) {
   EncodeTiled enc = encode_fn();
   if (!enc || rank < 1 || rank > 5) return false;
   cuuint64_t d[5], st[4];
@@ -637,7 +642,7 @@ bool encode_tensor_map_i32(CUtensorMap *map, const void *base, int rank, const u
     es[i] = 1;
     if (i + 1 < rank) st[i] = strides[i];
   }
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT32, rank, const_cast<void *>(base), d, st, bx, es,
+  CUresult r = enc(map, type, rank, const_cast<void *>(base), d, st, bx, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -709,6 +714,11 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
     Launch L(ctx, "inv_shots", s);
     inv_shots_kernel<<<256, 256, 0, s>>>(a.shots, wgt, B, ctx->d_status);
   }
+  // The tensor-core first pass writes its partials (below 729 x 2047 < 2^21)
+  // as split planes (3 bytes instead of 4) when the next pass is a TMA-staged
+  // store pass that reads them back.
+  const bool planes = !plan.empty() && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
+                      plan[1].mode == M_STORE && plan[1].in_t == T_I32 && ctx->generic_tma && plan[1].C % 32 == 0;
   const void *in = a.counts;
   size_t k_begin = 0, k_end = plan.size();
   if (a.stage != 0) {
@@ -734,10 +744,16 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
     CUtensorMap tmap, tmap_tail;
     const bool tensor = tensor_first_pass(ctx, pp, a);
-    if (tensor && make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(0)) &&
-        make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
-      lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), pp.r,
-                                     ctx->mma_biased, tile_begin, tile_end, s);
+    if (tensor) {
+      if (!make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(0)) ||
+          !make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
+        ctx->last_error = "tensor map of the counts rejected";
+        return LRE_ERR_CUDA;
+      }
+      const int64_t elems = ipow(6, pp.r - 6) * 4096;
+      int8_t *hi = planes ? static_cast<int8_t *>(out) + elems * 2 : nullptr;
+      lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), hi,
+                                     pp.r, ctx->mma_biased, tile_begin, tile_end, s);
       if (st != LRE_OK) return st;
     } else if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
         make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {
@@ -801,16 +817,21 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       gp.shots = (double)a.shots_uniform;
       gp.total = a.shots_uniform * B;
       gp.T = a.T;
-      for (int k = 0; k < 16; ++k) {
-        const double p3 = (double)ipow(3, k <= a.n ? k : 0);
-        gp.denom[k] = weighted ? p3 : (double)a.shots_uniform * p3;  // exact: < 2^53
-        gp.recip[k] = 1.0 / gp.denom[k];                              // host IEEE division
-        gp.dint[k] = weighted ? 0 : a.shots_uniform * ipow(3, k <= a.n ? k : 0);
-        gp.up3[k] = k <= a.n ? ipow(3, a.n - k) : 0;
+      for (int id = 0; id < 16; ++id) {  // id: number of identity letters
+        const double p3 = (double)ipow(3, id <= a.n ? id : 0);
+        gp.denom[id] = weighted ? p3 : (double)a.shots_uniform * p3;  // exact: < 2^53
+        gp.recip[id] = 1.0 / gp.denom[id];                              // host IEEE division
+        gp.dint[id] = weighted ? 0 : a.shots_uniform * ipow(3, id <= a.n ? id : 0);
+        gp.up3[id] = id <= a.n ? ipow(3, a.n - id) : 0;
       }
       gp.status = ctx->d_status;
-      lre_status tst = ctx->generic_tma ? tma_pass(ctx, gp, pp.J, pp.in_t, pp.acc_t, pp.mode, pp.weight, s)
+      const int in_t = (planes && k == 1) ? (int)T_I24P : pp.in_t;
+      lre_status tst = ctx->generic_tma ? tma_pass(ctx, gp, pp.J, in_t, pp.acc_t, pp.mode, pp.weight, s)
                                         : LRE_ERR_UNSUPPORTED;
+      if (tst == LRE_ERR_UNSUPPORTED && in_t == T_I24P) {
+        ctx->last_error = "split-plane partials need the TMA-staged second pass";
+        return LRE_ERR_UNSUPPORTED;
+      }
       if (tst == LRE_ERR_UNSUPPORTED) {
         int64_t blocks = (gp.items + 255) / 256;
         const int64_t cap = (int64_t)ctx->num_sms * 64;

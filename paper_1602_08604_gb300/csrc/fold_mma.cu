@@ -84,8 +84,8 @@ __device__ __forceinline__ int32_t d_to_int(uint32_t bits, float scale, int32_t 
 template <bool BIASED>
 __global__ void __launch_bounds__(MMA_THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
-                    const uint4 *__restrict__ gA, int32_t *__restrict__ out, int n, int64_t tile_begin,
-                    int64_t tile_end, int *status) {
+                    const uint4 *__restrict__ gA, int32_t *__restrict__ out, int8_t *__restrict__ out_hi, int n,
+                    int64_t tile_begin, int64_t tile_end, int *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *Am = smem;
@@ -251,9 +251,19 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
       sm103::tc_fence_before();
       sm103::mbar_arrive(&tile_free[pair]);
       const int64_t tile = tile_begin + blockIdx.x + lt * gridDim.x;
-      int32_t *o = out + tile * 4096 + plA;
+      if (out_hi) {  // split planes: low 16 bits, then the (signed) bits above
+        unsigned short *lo = reinterpret_cast<unsigned short *>(out) + tile * 4096 + plA;
+        signed char *hi = reinterpret_cast<signed char *>(out_hi) + tile * 4096 + plA;
 #pragma unroll
-      for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
+        for (int p = 0; p < 64; ++p) {
+          __stcs(lo + p * 64, (unsigned short)(acc[p] & 0xFFFF));
+          __stcs(hi + p * 64, (signed char)(acc[p] >> 16));
+        }
+      } else {
+        int32_t *o = out + tile * 4096 + plA;
+#pragma unroll
+        for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
+      }
     }
   }
   sm103::tc_fence_before();
@@ -299,19 +309,23 @@ uint32_t mma_box_rows(int which) { return which ? BOX_TAIL : BOX_BIG; }
 int64_t mma_max_count(int biased) { return biased ? 1023 : 2047; }
 
 // Launch the tensor-core first pass over tiles [tile_begin, tile_end) of an
-// n-qubit int16 count matrix (tile = ah * 2^(n-6) + oh).  map_big / map_tail
+// n-qubit int16 count matrix (tile = ah * 2^(n-6) + oh).  out_hi == nullptr:
+// int32 partials at out; otherwise split planes, the low 16 bits at out (as
+// uint16) and the bits above at out_hi (int8), exact while every partial is
+// below 2^23 in magnitude (729 x 2047 < 2^21 here).  map_big / map_tail
 // are tensor maps of the counts with boxes of 216 / 81 rows x 64 outcomes;
 // a_dev holds the operand written by mma_operand_upload; every count must be
 // at most mma_max_count(biased).
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
-                          int32_t *out, int n, int biased, int64_t tile_begin, int64_t tile_end, cudaStream_t s) {
+                          int32_t *out, int8_t *out_hi, int n, int biased, int64_t tile_begin, int64_t tile_end,
+                          cudaStream_t s) {
   const int64_t tiles = tile_end - tile_begin;
   if (tiles <= 0) return LRE_OK;
   const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
   Launch L(ctx, "fold_first6_mma", s);
   auto kern = biased ? fold_first6_mma<true> : fold_first6_mma<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
-  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, n,
+  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, out_hi, n,
                                            tile_begin, tile_end, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");

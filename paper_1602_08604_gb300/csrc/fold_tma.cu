@@ -35,19 +35,25 @@ __host__ __device__ constexpr int tma_warps() {
   return J == 3 ? 4 : 16;
 }
 
-template <int J>
+// box bytes per task: int32 values, or split planes (2 + 1 bytes per value)
+template <int J, bool PLANES = false>
 __host__ __device__ constexpr int box_bytes() {
-  return (J == 1 ? 3 : J == 2 ? 9 : 27) * (1 << J) * TC * 4;
+  return (J == 1 ? 3 : J == 2 ? 9 : 27) * (1 << J) * TC * (PLANES ? 3 : 4);
 }
 
-template <int J, typename AccT, int MODE>
+// PLANES: the input is split planes (map: the uint16 low halves, map_hi: the
+// int8 high parts, one box of each per task on the same barrier).
+template <int J, typename AccT, int MODE, bool PLANES>
 __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_constant__ CUtensorMap map,
+                                                                    const __grid_constant__ CUtensorMap map_hi,
                                                                     GenParams P) {
   constexpr int TMA_WARPS = tma_warps<J>();
   constexpr int NA = (J == 1) ? 3 : (J == 2) ? 9 : 27;
   constexpr int NO = 1 << J;
   constexpr int NP = 1 << (2 * J);
-  constexpr int BOX = box_bytes<J>();
+  constexpr int BOX = box_bytes<J, PLANES>();
+  constexpr int BOX_LO = NA * NO * TC * 2;  // PLANES: the uint16 box, then the int8 box
+  static_assert(!PLANES || BOX_LO % 128 == 0, "TMA destinations stay 128-byte aligned");
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128u - (sm103::smem_addr(smem_raw) & 127u)) & 127u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -73,6 +79,8 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
     const int64_t ah = ahoh / P.n_oh, oh = ahoh - ah * P.n_oh;
     sm103::mbar_arrive_expect_tx(&bar[b], BOX);
     sm103::tma_load_5d(buf + b * BOX, &map, (int)(cb * TC), 0, (int)oh, 0, (int)ah, &bar[b]);
+    if constexpr (PLANES)
+      sm103::tma_load_5d(buf + b * BOX + BOX_LO, &map_hi, (int)(cb * TC), 0, (int)oh, 0, (int)ah, &bar[b]);
   };
   if (lane == 0 && first < tasks) issue(first, 0);
   int64_t i = 0;
@@ -91,6 +99,8 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
       break;
     }
     const int32_t *S = reinterpret_cast<const int32_t *>(buf + b * BOX);
+    const unsigned short *SL = reinterpret_cast<const unsigned short *>(buf + b * BOX);
+    const signed char *SH = reinterpret_cast<const signed char *>(buf + b * BOX + BOX_LO);
     AccT acc[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) acc[p] = 0;
@@ -98,7 +108,13 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
     for (int al = 0; al < NA; ++al) {
       AccT v[NO];
 #pragma unroll
-      for (int ol = 0; ol < NO; ++ol) v[ol] = (AccT)S[(al * NO + ol) * TC + lane];
+      for (int ol = 0; ol < NO; ++ol) {
+        const int idx = (al * NO + ol) * TC + lane;
+        if constexpr (PLANES)
+          v[ol] = (AccT)(int32_t)(((uint32_t)(int32_t)SH[idx] << 16) | (uint32_t)SL[idx]);
+        else
+          v[ol] = (AccT)S[idx];
+      }
       wht<J>(v);
 #pragma unroll
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
@@ -119,17 +135,18 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
   __syncwarp();
 }
 
-template <int J, typename AccT, int MODE>
-lre_status launch(lre_ctx *ctx, const CUtensorMap &map, const GenParams &P, cudaStream_t s) {
+template <int J, typename AccT, int MODE, bool PLANES = false>
+lre_status launch(lre_ctx *ctx, const CUtensorMap &map, const CUtensorMap &map_hi, const GenParams &P,
+                  cudaStream_t s) {
   constexpr int TMA_WARPS = tma_warps<J>();
-  constexpr int smem = TMA_WARPS * 2 * box_bytes<J>() + TMA_WARPS * 16 + 16 + 128;
-  auto k = fold_tma<J, AccT, MODE>;
+  constexpr int smem = TMA_WARPS * 2 * box_bytes<J, PLANES>() + TMA_WARPS * 16 + 16 + 128;
+  auto k = fold_tma<J, AccT, MODE, PLANES>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int64_t tasks = P.items / TC;
   int64_t grid = (tasks + TMA_WARPS - 1) / TMA_WARPS;
   const int64_t cap = (int64_t)ctx->num_sms * (smem <= 110 * 1024 ? 2 : 1);
   if (grid > cap) grid = cap;
-  k<<<(unsigned)grid, TMA_WARPS * 32, smem, s>>>(map, P);
+  k<<<(unsigned)grid, TMA_WARPS * 32, smem, s>>>(map, map_hi, P);
   return LRE_OK;
 }
 
@@ -137,35 +154,51 @@ lre_status launch(lre_ctx *ctx, const CUtensorMap &map, const GenParams &P, cuda
 
 lre_status passes::tma_pass(lre_ctx *ctx, const GenParams &P, int J, int in_t, int acc_t, int mode, bool weight,
                             cudaStream_t s) {
-  if (in_t != T_I32 || J < 1 || J > 3 || P.C % TC != 0 || weight) return LRE_ERR_UNSUPPORTED;
+  if ((in_t != T_I32 && in_t != T_I24P) || J < 1 || J > 3 || P.C % TC != 0 || weight) return LRE_ERR_UNSUPPORTED;
   // final passes (the correctly rounded division of every coefficient) are
   // ALU-bound and run faster in the register-load kernel at full occupancy
   if (mode != M_STORE && mode != M_PARITY) return LRE_ERR_UNSUPPORTED;
   if (acc_t != T_I32 && acc_t != T_I64) return LRE_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(P.in) & 15) != 0) return LRE_ERR_UNSUPPORTED;
+  const bool planes = in_t == T_I24P;
+  if (planes && (J != 3 || mode != M_STORE || acc_t != T_I32)) return LRE_ERR_UNSUPPORTED;
   const int NA = J == 1 ? 3 : J == 2 ? 9 : 27, NO = 1 << J;
   const int64_t n_ah = ipow(3, P.r - J);
   // X[ah][al][oh][ol][c], innermost first
   const uint64_t dims[5] = {(uint64_t)P.C, (uint64_t)NO, (uint64_t)P.n_oh, (uint64_t)NA, (uint64_t)n_ah};
-  const uint64_t e = 4;
-  const uint64_t strides[4] = {(uint64_t)P.C * e, (uint64_t)P.C * NO * e, (uint64_t)P.C * NO * P.n_oh * e,
-                               (uint64_t)P.C * NO * P.n_oh * NA * e};
   const uint32_t box[5] = {TC, (uint32_t)NO, 1, (uint32_t)NA, 1};
-  CUtensorMap map;
+  auto strides_of = [&](uint64_t e, uint64_t *st) {
+    st[0] = (uint64_t)P.C * e;
+    st[1] = (uint64_t)P.C * NO * e;
+    st[2] = (uint64_t)P.C * NO * P.n_oh * e;
+    st[3] = (uint64_t)P.C * NO * P.n_oh * NA * e;
+  };
+  CUtensorMap map, map_hi;
+  uint64_t strides[4];
+  if (planes) {
+    const uint64_t elems = (uint64_t)P.C * NO * P.n_oh * NA * n_ah;
+    strides_of(2, strides);
+    if (!encode_tensor_map(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, P.in, 5, dims, strides, box))
+      return LRE_ERR_UNSUPPORTED;
+    strides_of(1, strides);
+    if (!encode_tensor_map(&map_hi, CU_TENSOR_MAP_DATA_TYPE_UINT8, static_cast<const char *>(P.in) + elems * 2, 5,
+                           dims, strides, box))
+      return LRE_ERR_UNSUPPORTED;
+    Launch L(ctx, "fold_pass", s);
+    return launch<3, int32_t, M_STORE, true>(ctx, map, map_hi, P, s);
+  }
+  strides_of(4, strides);
   if (!encode_tensor_map_i32(&map, P.in, 5, dims, strides, box)) return LRE_ERR_UNSUPPORTED;
+  map_hi = map;
   Launch L(ctx, mode == M_STORE ? "fold_pass" : "fold_final", s);
   const bool i64 = acc_t == T_I64;
-#define LRE_TMA_CASE(JJ)                                                                          \
-  if (J == JJ) {                                                                                  \
-    switch (mode) {                                                                               \
-      case M_STORE:                                                                               \
-        return i64 ? launch<JJ, int64_t, M_STORE>(ctx, map, P, s) : launch<JJ, int32_t, M_STORE>(ctx, map, P, s); \
-      case M_PARITY:                                                                              \
-        return i64 ? launch<JJ, int64_t, M_PARITY>(ctx, map, P, s) : launch<JJ, int32_t, M_PARITY>(ctx, map, P, s); \
-      case M_FINAL_U:                                                                             \
-        return i64 ? launch<JJ, int64_t, M_FINAL_U>(ctx, map, P, s)                               \
-                   : launch<JJ, int32_t, M_FINAL_U>(ctx, map, P, s);                              \
-    }                                                                                             \
+#define LRE_TMA_CASE(JJ)                                                                                  \
+  if (J == JJ) {                                                                                          \
+    if (mode == M_STORE)                                                                                  \
+      return i64 ? launch<JJ, int64_t, M_STORE>(ctx, map, map_hi, P, s)                                   \
+                 : launch<JJ, int32_t, M_STORE>(ctx, map, map_hi, P, s);                                  \
+    return i64 ? launch<JJ, int64_t, M_PARITY>(ctx, map, map_hi, P, s)                                    \
+               : launch<JJ, int32_t, M_PARITY>(ctx, map, map_hi, P, s);                                   \
   }
   LRE_TMA_CASE(1)
   LRE_TMA_CASE(2)

@@ -117,6 +117,8 @@ int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a);
 // strides in bytes of dims 1..rank-1); false if the driver rejects it.
 bool encode_tensor_map_i32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
                            const uint64_t *strides, const uint32_t *box);
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, const void *base, int rank,
+                       const uint64_t *dims, const uint64_t *strides, const uint32_t *box);
 
 // ---- step (ii): theta -> rho -------------------------------------------------
 size_t assemble_workspace_bytes(int n);
@@ -155,7 +157,8 @@ uint32_t mma_box_rows(int which);    // TMA box rows: 0 the 216-row box, 1 the 8
 int64_t mma_max_count(int biased);   // largest count the operand encoding keeps exact
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
-                          int32_t *out, int n, int biased, int64_t tile_begin, int64_t tile_end, cudaStream_t s);
+                          int32_t *out, int8_t *out_hi, int n, int biased, int64_t tile_begin, int64_t tile_end,
+                          cudaStream_t s);
 
 // ---- batched instances (one persistent launch) ---------------------------------
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);

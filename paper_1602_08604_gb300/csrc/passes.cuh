@@ -20,7 +20,9 @@
 namespace lre {
 namespace passes {
 
-enum { T_I16 = 0, T_I32 = 1, T_I64 = 2, T_F64 = 3 };
+// T_I24P: int32 values stored as split planes, the low 16 bits (uint16) then
+// the bits above (int8), for partials below 2^23 in magnitude
+enum { T_I16 = 0, T_I32 = 1, T_I64 = 2, T_F64 = 3, T_I24P = 4 };
 enum { M_STORE = 0, M_FINAL_U = 1, M_FINAL_W = 2, M_PARITY = 3 };
 
 // Pauli-digit index of a pass block: digit q is m_q ? a_q + 1 : 0 (a_q the
