@@ -179,7 +179,12 @@ lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_base
  * `stream`.  The call returns when theta (and rho) are in host memory, with
  * any latched kernel error.  Device memory used: the counts (3^n 2^n x 2 or
  * 4 bytes), theta, rho and the fold workspace, all held in the context's
- * workspace. */
+ * workspace.  When a workspace limit (lre_set_workspace_limit) leaves no
+ * room for the dense counts, shot records with at most 2047 shots per basis
+ * (a multiple of 8) take a path without them: each chunk's records are
+ * grouped by count tile on the device and the tensor-core first pass builds
+ * its count tiles from them in shared memory (slower on states whose shots
+ * concentrate on few outcomes; same results). */
 lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind host_kind,
                              int64_t shots_uniform, int n, double *theta_host, lre_c64 *rho_host,
                              lre_stream stream);

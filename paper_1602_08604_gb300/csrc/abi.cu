@@ -413,6 +413,16 @@ extern "C" lre_status lre_debug_set_generic_tma(lre_ctx *ctx, int on) {
   return LRE_OK;
 }
 
+// Test hook (not part of include/lre.h): lre_estimate_host with shot records
+// takes the records-fed tensor-core first pass (no dense device counts)
+// whenever it applies (1), or only when the workspace limit requires it (0,
+// the default).
+extern "C" lre_status lre_debug_set_records_direct(lre_ctx *ctx, int on) {
+  if (!ctx || on < 0 || on > 1) return LRE_ERR_INVALID_ARG;
+  ctx->records_direct = on;
+  return LRE_OK;
+}
+
 // Test hook (not part of include/lre.h): bytes of host input per streamed
 // chunk of lre_estimate_host (rounded to whole tile rows where the first pass
 // runs per chunk); small values exercise many chunks on small inputs.

@@ -691,6 +691,13 @@ int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a) {
   return (tensor_first_pass(ctx, plan[0], a) || ctx->first_variant >= 1) ? 729 : 0;
 }
 
+bool fold_first_is_tensor(lre_ctx *ctx, const FoldArgs &a) {
+  if (a.shots) return false;
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(a.counts) & 15) == 0;
+  auto plan = make_plan(a.n, a.kind, false, a.S != nullptr, a.shots_uniform, aligned16, ctx->first_variant);
+  return !plan.empty() && tensor_first_pass(ctx, plan[0], a);
+}
+
 lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
   const bool weighted = a.shots != nullptr;
   const bool parity = a.S != nullptr;
@@ -744,7 +751,14 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       out = parity ? static_cast<void *>(a.S) : static_cast<void *>(a.theta);
     CUtensorMap tmap, tmap_tail;
     const bool tensor = tensor_first_pass(ctx, pp, a);
-    if (tensor) {
+    if (tensor && a.rec_entries) {
+      if (a.stage != 1) return LRE_ERR_INVALID_ARG;
+      const int64_t elems = ipow(6, pp.r - 6) * 4096;
+      int8_t *hi = planes ? static_cast<int8_t *>(out) + elems * 2 : nullptr;
+      lre_status st = mma_first_pass_records(ctx, ctx->mma_operand, a.rec_entries, a.rec_offs, a.shots_uniform,
+                                             static_cast<int32_t *>(out), hi, pp.r, tile_begin, tile_end, s);
+      if (st != LRE_OK) return st;
+    } else if (tensor) {
       if (!make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(0)) ||
           !make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
         ctx->last_error = "tensor map of the counts rejected";

@@ -81,11 +81,22 @@ __device__ __forceinline__ int32_t d_to_int(uint32_t bits, float scale, int32_t 
   return __float_as_int(fmaf(__uint_as_float(bits), scale, 12582912.f)) - 0x4B400000 - sub;
 }
 
-template <bool BIASED>
+// RECORDS: the count tiles are built in shared memory from shot records
+// grouped by tile and chunk (records.cu: entries (al << 6) | ol per tile
+// row, bucket starts in offs, bucket = oh * 2 + chunk) instead of being
+// loaded by TMA: warps 0, 2 and 3 each own one ring slot; once the MMAs of
+// the slot's previous chunk are done they clear it (only the cells that chunk
+// set, when it was sparse), add the bucket's entries with packed 16-bit
+// shared-memory atomics (eight loads in flight per lane), make the
+// writes visible to the tensor cores (proxy fence) and arrive on the slot.
+// Tile rows are numbered from tile_begin / 2^(n-6) in entries and offs.
+template <bool BIASED, bool RECORDS>
 __global__ void __launch_bounds__(MMA_THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
                     const uint4 *__restrict__ gA, int32_t *__restrict__ out, int8_t *__restrict__ out_hi, int n,
-                    int64_t tile_begin, int64_t tile_end, int *status) {
+                    int64_t tile_begin, int64_t tile_end, const uint16_t *__restrict__ entries,
+                    const int32_t *__restrict__ offs, int64_t shots, int *status) {
+  static_assert(!(BIASED && RECORDS), "records feed the raw-count operand");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *Am = smem;
@@ -128,7 +139,63 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int64_t total = my_tiles * 2;  // chunks of this CTA
 
-  if (warp == 0) {
+  if (RECORDS && (warp == 0 || warp == 2 || warp == 3)) {
+    const int bw = warp == 0 ? 0 : warp - 1;  // builder of chunks g = bw (mod 3): always slot bw
+    const int64_t tr0 = tile_begin / n_oh;
+    const int64_t row_entries = 729 * shots;
+    const int nb = (int)(2 * n_oh);  // buckets per tile row: (oh, chunk)
+    constexpr int32_t SPARSE = 2048;  // re-zero only the touched cells below this many entries
+    uint4 *slot4 = reinterpret_cast<uint4 *>(ring + bw * SLOT_BYTES);
+    uint32_t *slot32 = reinterpret_cast<uint32_t *>(ring + bw * SLOT_BYTES);
+    const uint16_t *pent = nullptr;  // the slot's previous chunk: its entries and row base
+    int32_t pe0 = 0, pe1 = -1;
+    int pbase = 0;
+    for (int64_t g = bw; g < total; g += MMA_R) {
+      const int64_t tile = tile_begin + blockIdx.x + (g >> 1) * gridDim.x;
+      const int c = (int)(g & 1);
+      const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
+      if (g >= MMA_R && !sm103::mbar_wait(&empty[bw], (uint32_t)((g / MMA_R - 1) & 1), abort_flag)) {
+        give_up();
+        break;
+      }
+      if (pent && pe1 - pe0 <= SPARSE) {  // zero the cells the previous chunk set
+        for (int32_t e = pe0 + lane; e < pe1; e += 32 * 8) {
+          uint32_t v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = e + 32 * k < pe1 ? (uint32_t)__ldcs(pent + e + 32 * k) : 0xFFFFFFFFu;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (v[k] != 0xFFFFFFFFu) slot32[((uint32_t)((int)(v[k] >> 6) - pbase) * 64 + (v[k] & 63u)) >> 1] = 0u;
+        }
+      } else {
+        for (int k = lane; k < CHUNK_ROWS * 8; k += 32) slot4[k] = make_uint4(0, 0, 0, 0);
+      }
+      __syncwarp();
+      const uint16_t *ent = entries + (ah - tr0) * row_entries;
+      const int32_t *of = offs + (ah - tr0) * nb;
+      const int bk = (int)(oh * 2 + c);
+      const int32_t e0 = of[bk], e1 = bk + 1 < nb ? of[bk + 1] : (int32_t)row_entries;
+      const int base = c * 432;
+      for (int32_t e = e0 + lane; e < e1; e += 32 * 8) {
+        uint32_t v[8];  // eight independent loads in flight per lane, then their adds
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = e + 32 * k < e1 ? (uint32_t)__ldcs(ent + e + 32 * k) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (v[k] != 0xFFFFFFFFu) {
+            const uint32_t idx = (uint32_t)((int)(v[k] >> 6) - base) * 64 + (v[k] & 63u);
+            atomicAdd(&slot32[idx >> 1], 1u << ((idx & 1u) << 4));
+          }
+      }
+      sm103::fence_proxy_async_smem();  // the tensor cores read what this warp wrote
+      __syncwarp();
+      if (lane == 0) sm103::mbar_arrive(&full[bw]);
+      pent = ent;
+      pe0 = e0;
+      pe1 = e1;
+      pbase = base;
+    }
+  } else if (warp == 0) {
     if (lane == 0) {
       int64_t g = 0;
       for (; g < total && !*abort_flag; ++g) {
@@ -194,7 +261,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
         if (sm103::mbar_try_wait(&empty[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
     }
   } else if (warp == 2 || warp == 3) {
-    if constexpr (BIASED) {
+    if constexpr (BIASED && !RECORDS) {
       for (int64_t g = 0; g < total; ++g) {
         const int slot = (int)(g % MMA_R);
         if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
@@ -323,10 +390,30 @@ lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtens
   if (tiles <= 0) return LRE_OK;
   const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
   Launch L(ctx, "fold_first6_mma", s);
-  auto kern = biased ? fold_first6_mma<true> : fold_first6_mma<false>;
+  auto kern = biased ? fold_first6_mma<true, false> : fold_first6_mma<false, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
   kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, out_hi, n,
-                                           tile_begin, tile_end, ctx->d_status);
+                                           tile_begin, tile_end, nullptr, nullptr, 0, ctx->d_status);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
+}
+
+// The same pass over tiles [tile_begin, tile_end) whose counts come from shot
+// records grouped by tile (tile_bucket_run over the tile rows from
+// tile_begin / 2^(n-6) on); every count must be at most 2047.
+lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_t *entries, const int32_t *offs,
+                                  int64_t shots, int32_t *out, int8_t *out_hi, int n, int64_t tile_begin,
+                                  int64_t tile_end, cudaStream_t s) {
+  const int64_t tiles = tile_end - tile_begin;
+  if (tiles <= 0) return LRE_OK;
+  if (shots > mma_max_count(0)) return LRE_ERR_UNSUPPORTED;
+  const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
+  CUtensorMap unused{};
+  Launch L(ctx, "fold_first6_mma_records", s);
+  auto kern = fold_first6_mma<false, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
+  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(unused, unused, static_cast<const uint4 *>(a_dev), out, out_hi, n,
+                                           tile_begin, tile_end, entries, offs, shots, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }

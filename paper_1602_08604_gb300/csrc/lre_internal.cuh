@@ -55,6 +55,7 @@ struct lre_ctx {
   int batch_occupancy[2] = {0, 0};  // most resident CTAs per SM of batch_kernel<2>, <3>
   std::vector<lre_batch_entry> batch_cache;  // device pass tables of earlier batched calls
   size_t host_chunk_bytes = 256ull << 20; // host-input streaming: bytes of input per chunk
+  int records_direct = 0;                 // host shot records: 1 = always the records-fed first pass
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
@@ -105,6 +106,10 @@ struct FoldArgs {
   // every pass after it (the first pass's output already in the workspace).
   int stage = 0;
   int64_t ah_begin = 0, ah_end = -1;
+  // stage 1 only: counts from shot records grouped by tile (tile_bucket_run
+  // over tile rows ah_begin..ah_end) instead of dense counts
+  const uint16_t *rec_entries = nullptr;
+  const int32_t *rec_offs = nullptr;
 };
 size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound,
                             int variant = 2);
@@ -112,6 +117,9 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
 // Basis rows per unit of the stage-1 split (729), or 0 when these arguments
 // cannot be split (no six-qubit first pass, or one without tile ranges).
 int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a);
+// True when the first pass for these arguments is the tensor-core one (the
+// one that can take its counts from bucketed shot records).
+bool fold_first_is_tensor(lre_ctx *ctx, const FoldArgs &a);
 
 // Tiled TMA descriptor of an int32 tensor (dims and box innermost first,
 // strides in bytes of dims 1..rank-1); false if the driver rejects it.
@@ -156,6 +164,12 @@ size_t mma_operand_bytes();
 uint32_t mma_box_rows(int which);    // TMA box rows: 0 the 216-row box, 1 the 81-row tail
 int64_t mma_max_count(int biased);   // largest count the operand encoding keeps exact
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
+// records grouped by count tile (records.cu) and the first pass over them
+lre_status tile_bucket_run(lre_ctx *ctx, const uint16_t *records, int64_t tile_rows, int64_t shots, int n,
+                           uint16_t *entries, int32_t *offs, cudaStream_t s);
+lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_t *entries, const int32_t *offs,
+                                  int64_t shots, int32_t *out, int8_t *out_hi, int n, int64_t tile_begin,
+                                  int64_t tile_end, cudaStream_t s);
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
                           int32_t *out, int8_t *out_hi, int n, int biased, int64_t tile_begin, int64_t tile_end,
                           cudaStream_t s);

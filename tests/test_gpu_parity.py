@@ -268,3 +268,47 @@ def test_assemble_tiled_passes_sampled(env, n):
     tr = torch.diagonal(rho).sum().item()
     assert abs(tr - 1) < 1e-4
     assert torch.equal(rho, rho.conj().T)             # exactly Hermitian
+
+
+@pytest.mark.parametrize("n,chunk,mode", [(9, 1, "forced"), (10, 3000000, "forced"), (8, 0, "forced"),
+                                          (10, 3000000, "limit")])
+def test_estimate_host_records_without_dense_counts(env, n, chunk, mode):
+    """Shot records folded by the tensor-core first pass from tile-grouped
+    records (no dense device counts), forced by the test hook or chosen
+    because the workspace limit leaves no room for the dense counts: the same
+    bits as the device path and the oracle."""
+    torch, lre, ctx0 = env
+    import ctypes
+    from synth import gen
+    ctx = lre.lre_create(0)
+    L = lre.load()
+    hooks = {}
+    for name in ("lre_debug_set_host_chunk", "lre_debug_set_records_direct"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int64 if name.endswith("chunk") else ctypes.c_int]
+        f.restype = ctypes.c_int
+        hooks[name] = f
+    try:
+        N = 1000
+        assert hooks["lre_debug_set_host_chunk"](ctx, chunk if chunk else 256 << 20) == 0
+        if mode == "forced":
+            assert hooks["lre_debug_set_records_direct"](ctx, 1) == 0
+        else:
+            lre.lre_set_workspace_limit(ctx, 100 << 20)  # room for the records path, not for dense counts
+        rec_dev = torch.empty((3 ** n, N), dtype=torch.int16, device="cuda")
+        gen.gen_ghz_records(n, 0.05, 77 + n, rec_dev)
+        rec = rec_dev.cpu().numpy().view(np.uint16)
+        host_in = torch.from_numpy(rec.view(np.int16)).pin_memory()
+        counts = np.stack([np.bincount(r, minlength=2 ** n) for r in rec.astype(np.int64)]).astype(np.int32)
+        th = torch.empty(4 ** n, dtype=torch.float64).pin_memory()
+        rh = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64).pin_memory()
+        lre.lre_profile(ctx, True)
+        lre.lre_estimate_host(ctx, host_in, lre.LRE_HOST_RECORDS_U16, N, n, th, rh)
+        names = {k for k, _ in lre.lre_profile_records(ctx)}
+        lre.lre_profile(ctx, False)
+        assert "fold_first6_mma_records" in names and "histogram" not in names, names
+        t_ref = direct.estimate(counts, N, n)
+        np.testing.assert_array_equal(th.numpy(), t_ref)
+        assert rel_fro(rh.numpy(), direct.mu(t_ref, n)) <= 1e-6
+    finally:
+        lre.lre_destroy(ctx)
