@@ -180,9 +180,14 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict_
       const int64_t item = (s_unit - P.unit_begin) * 256 + threadIdx.x;
       if (item < P.items) run_item<JMAX>(P, item);
     }
-    __threadfence();
+    // publish the unit: the CTA barrier orders every thread's writes before
+    // thread 0's device-scope fence, which orders them before the counter
+    // the dependent units acquire (the usual grid-barrier pattern)
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(done + p, 1u);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(done + p, 1u);
+    }
   }
 }
 
