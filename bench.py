@@ -562,6 +562,55 @@ def run_batched(args):
     return out
 
 
+def accuracy_point(lre, ctx, torch, n, shots, seed):
+    """One point of the Sec. V / Fig. 3 study: the maximally mixed n-qubit
+    state measured with `shots` shots per basis (counts drawn on the device as
+    a product of unpolarised qubits; int32 above 32767 shots), through lre_estimate and
+    lre_project.  For the true state I/d every error needs only theta and
+    spectra: ||mu - I/d||_F^2 = sum_{P != I} t_P^2 / d, ||rho_hat - I/d||_F^2 =
+    sum (l_i - 1/d)^2 and the fidelity with I/d = (sum sqrt(l_i))^2 / d."""
+    import numpy as np
+    from synth import gen
+    d = 2 ** n
+    dev = torch.device("cuda", 0)
+    counts = torch.empty((3 ** n, d), dtype=torch.int16 if shots <= 32767 else torch.int32, device=dev)
+    gen.gen_product(np.zeros((n, 3)), shots, seed, counts)
+    theta = torch.empty(4 ** n, dtype=torch.float64, device=dev)
+    rho = torch.empty((d, d), dtype=torch.complex64, device=dev)
+    lre.lre_estimate(ctx, counts, shots, n, theta, rho)
+    del counts
+    rho_p = torch.empty_like(rho)
+    eig = torch.empty(d, dtype=torch.float64, device=dev)
+    lre.lre_project(ctx, rho, n, rho_p, eig_rho=eig)
+    lre.lre_sync(ctx)
+    hs_mu = float((theta[1:] ** 2).sum().item() / d)
+    lam = eig.clamp(min=0.0)
+    hs_rho = float(((eig - 1.0 / d) ** 2).sum().item())
+    fid = float(lam.sqrt().sum().item() ** 2 / d)
+    n0 = shots / d  # shots per basis = 2^n N_0 (N = 6^n N_0 copies in all)
+    want = ((10.0 / 3.0) ** n - 3.0 ** (-n)) / (d * shots)
+    return {"shots_per_basis": shots, "N0": n0, "hs_mu": hs_mu, "hs_mu_expected": want,
+            "hs_mu_ratio": hs_mu / want, "paper_hs_law": (5.0 / 6.0) ** n / n0,
+            "hs_rho_hat": hs_rho, "infidelity_rho_hat": 1.0 - fid,
+            "paper_infidelity_law": (5.0 / 3.0) ** n / (4.0 * n0),
+            "kept_eigenvalues": int((eig > 0).sum().item()), "theta_I": float(theta[0].item())}
+
+
+def run_accuracy(args):
+    """Sec. V / Fig. 3 analogue on the GPU: estimation error against shots
+    for the maximally mixed state (the paper's own workload), one JSON line."""
+    import torch
+    from paper_1602_08604_gb300 import lre
+    ctx = lre.lre_create(0)
+    try:
+        pts = [accuracy_point(lre, ctx, torch, args.study_n, s, 1000 + i)
+               for i, s in enumerate(args.study_shots)]
+    finally:
+        lre.lre_destroy(ctx)
+    return {"study": "estimation error vs shots, maximally mixed state (Sec. V, Fig. 3)", "n": args.study_n,
+            "data": "synthetic", "expected": "E||mu - rho||_F^2 = ((10/3)^n - 3^-n)/(d S)", "points": pts}
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -591,7 +640,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="n14", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default="n14", choices=sorted(WORKLOADS) + ["batched", "accuracy"])
+    ap.add_argument("--study-n", type=int, default=12, help="qubits of the accuracy study")
+    ap.add_argument("--study-shots", type=int, nargs="+", default=[128, 256, 512, 1024, 2047],
+                    help="shots per basis of the accuracy study's points")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -603,6 +655,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     args = ap.parse_args()
+    if args.workload == "accuracy":
+        out = run_accuracy(args) if args.impl == "ours" else None
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
     if args.workload == "batched":
         out = run_batched(args) if args.impl == "ours" else None
         if out is not None:
