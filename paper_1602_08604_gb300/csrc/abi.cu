@@ -386,8 +386,8 @@ uint64_t lre_launch_count(lre_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 }  // extern "C"
 
-// Test hook (not part of include/lre.h): choose the first fold pass of later
-// calls on this context: 0 register kernel, 1 TMA pipeline (the default), 2
+// Test hook (not part of include/lre.h): choose the ALU first fold pass of
+// later calls on this context: 0 register kernel, 1 TMA pipeline (the default), 2
 // TMA pipeline fused with the second pass where the plan allows.
 extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   if (!ctx || variant < 0 || variant > 2) return LRE_ERR_INVALID_ARG;

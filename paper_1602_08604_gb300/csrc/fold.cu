@@ -20,6 +20,17 @@
 // and after it
 //     Y[ah][oh][pl][c],       pl in 4^J,
 // so the last pass leaves theta in the canonical order of Eq. (5).
+//
+// Which kernel runs which pass (fold_run):
+//   first pass, int16 counts of at most 2047 shots: fold_first6_mma
+//     (fold_mma.cu, tensor cores; split-plane partials when the next pass is
+//     TMA-staged), or its records-fed form for lre_estimate_host;
+//   first pass otherwise: fold_first6_pipe below (TMA pipeline on the ALU),
+//     fold_first6 (register kernel, test hook) or the fused variant;
+//   later store/parity passes: fold_tma (fold_tma.cu, TMA-staged) where the
+//     columns allow, else fold_generic below;
+//   the final pass: fold_generic with the divisor tables in shared memory
+//     (the correctly rounded division in passes.cuh is ALU/FP64-bound).
 #include <cuda_runtime.h>
 
 #include <cudaTypedefs.h>
@@ -121,7 +132,8 @@ __global__ void __launch_bounds__(P1_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
-// The same first pass as a warp-specialised TMA pipeline (the default).
+// The same first pass as a warp-specialised TMA pipeline (the ALU first pass
+// wherever the tensor-core one, fold_mma.cu, does not apply).
 //   warp 0      producer: one 2D TMA load per sub-tile (81 rows x 64
 //               outcomes = the two top ternary digits of the tile fixed) into
 //               a ring of R shared-memory slots, completion on mbarriers.

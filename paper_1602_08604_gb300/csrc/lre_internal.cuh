@@ -41,7 +41,7 @@ struct lre_ctx {
   std::vector<lre_prof_entry> prof_pool;  // reused events
   size_t prof_used = 0;
   uint64_t launches = 0;                  // kernels of this library launched so far
-  // first fold pass: 0 register kernel, 1 TMA pipeline (default), 2 TMA
+  // ALU first fold pass: 0 register kernel, 1 TMA pipeline (default), 2 TMA
   // pipeline fused with the second pass through L2 (correct, but slower on
   // GB300 so far: its second-pass jobs are L2-latency bound)
   int first_variant = 1;
