@@ -211,7 +211,8 @@ lre_status lre_estimate_host(lre_ctx *ctx, const void *host_in, lre_host_kind ho
 lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream);
 
 /* Autotuner for lre_batch_run: times the candidate schedules (qubits per
- * fold pass 2 or 3; 1, 2 or 4 resident CTAs per SM) on this batch, keeps the
+ * fold pass 2 or 3; 1 or 2 resident CTAs per SM; 256 or 1024 items per work
+ * unit of the count-reading first passes) on this batch, keeps the
  * fastest in the context for later lre_batch_run calls, and returns its time
  * per launch in *best_ms (may be NULL).  Synchronises `stream`. */
 lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream,

@@ -41,7 +41,8 @@ struct BPhase {
   int code;
   int dep;          // index of the phase this one waits for (-1: none)
   unsigned dep_units;
-  int per_unit;     // items per work unit: 256 (one per thread) or 1 (a shared-memory block)
+  int per_unit;     // items per work unit: a multiple of 256 (each thread takes every 256th), or 1 (a
+                    // shared-memory block)
   int64_t unit_begin, units, items;
   GenParams g;
   AsmParams a;
@@ -177,8 +178,11 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict_
       else
         asm_low6_block<NumI64, false>(in, P.a.out, blk, tile, P.a.scale);
     } else {
-      const int64_t item = (s_unit - P.unit_begin) * 256 + threadIdx.x;
-      if (item < P.items) run_item<JMAX>(P, item);
+      const int64_t first = (s_unit - P.unit_begin) * P.per_unit + threadIdx.x;
+      for (int k = 0; k < P.per_unit; k += 256) {
+        const int64_t item = first + k;
+        if (item < P.items) run_item<JMAX>(P, item);
+      }
     }
     // publish the unit: the CTA barrier orders every thread's writes before
     // thread 0's device-scope fence, which orders them before the counter
@@ -201,7 +205,7 @@ struct Plan {
 
 // Per-instance pass lists, workspace offsets relative to `base`, then the
 // pass-major global order.
-Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
+Plan build_plan(const lre_instance *inst, int count, int jmax, int first_unit, char *base) {
   std::vector<std::vector<BPhase>> per(count);
   size_t off = 0;
   for (int i = 0; i < count; ++i) {
@@ -271,7 +275,9 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, char *base) {
         g.up3[kk] = kk <= n ? ipow(3, n - kk) : 0;
       }
       b.items = g.items;
-      b.per_unit = 256;
+      // count-reading first passes do the most work per item; larger units
+      // there amortise the claim, wait and publish of a unit
+      b.per_unit = k == 0 ? first_unit : 256;
       per[i].push_back(b);
       in = g.out;
     }
@@ -365,7 +371,7 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   const bool capturing = cap != cudaStreamCaptureStatusNone;
   const int jmax = ctx->batch_jmax;
   // layout: [BatchState][done counters][phase table][instance workspaces]
-  Plan probe = build_plan(inst, count, jmax, nullptr);
+  Plan probe = build_plan(inst, count, jmax, ctx->batch_first_unit, nullptr);
   const size_t nph = probe.phases.size();
   const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) +
                       up256(nph * (sizeof(BPhase) + sizeof(int64_t)));
@@ -378,7 +384,7 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   BatchState *bs = reinterpret_cast<BatchState *>(w);
   unsigned *done = reinterpret_cast<unsigned *>(w + up256(sizeof(BatchState)));
   BPhase *dph = reinterpret_cast<BPhase *>(w + up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)));
-  Plan plan = build_plan(inst, count, jmax, w + head);
+  Plan plan = build_plan(inst, count, jmax, ctx->batch_first_unit, w + head);
   for (auto &b : plan.phases) b.g.status = ctx->d_status;
   // The pass table (phases, then their first units) lives in a device buffer
   // per distinct table (kept until lre_destroy), so a captured launch reads a
@@ -459,32 +465,38 @@ lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStr
   lre_status st = validate(inst, count);
   if (st != LRE_OK) return st;
   const int cand_j[2] = {2, 3};
-  const int cand_occ[3] = {1, 2, 4};
+  const int cand_occ[2] = {1, 2};       // resident CTAs per SM (the kernel fits at most two)
+  const int cand_unit[2] = {256, 1024};  // items per unit of the count-reading first passes
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     return LRE_ERR_CUDA;
   }
   float best = 1e30f;
-  int bj = ctx->batch_jmax, bo = ctx->batch_ctas_per_sm;
+  int bj = ctx->batch_jmax, bo = ctx->batch_ctas_per_sm, bu = ctx->batch_first_unit;
   for (int j : cand_j) {
     for (int o : cand_occ) {
-      ctx->batch_jmax = j;
-      ctx->batch_ctas_per_sm = o;
-      if ((st = batch_run(ctx, inst, count, s)) != LRE_OK) break;  // warm-up
-      cudaEventRecord(e0, s);
-      for (int rep = 0; rep < 3 && st == LRE_OK; ++rep) st = batch_run(ctx, inst, count, s);
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) st = LRE_ERR_CUDA;
-      if (st != LRE_OK) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= 3.f;
-      if (ms < best) {
-        best = ms;
-        bj = j;
-        bo = o;
+      for (int u : cand_unit) {
+        ctx->batch_jmax = j;
+        ctx->batch_ctas_per_sm = o;
+        ctx->batch_first_unit = u;
+        if ((st = batch_run(ctx, inst, count, s)) != LRE_OK) break;  // warm-up
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3 && st == LRE_OK; ++rep) st = batch_run(ctx, inst, count, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = LRE_ERR_CUDA;
+        if (st != LRE_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (ms < best) {
+          best = ms;
+          bj = j;
+          bo = o;
+          bu = u;
+        }
       }
+      if (st != LRE_OK) break;
     }
     if (st != LRE_OK) break;
   }
@@ -492,6 +504,7 @@ lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStr
   cudaEventDestroy(e1);
   ctx->batch_jmax = bj;
   ctx->batch_ctas_per_sm = bo;
+  ctx->batch_first_unit = bu;
   if (best_ms) *best_ms = best;
   return st;
 }
