@@ -370,64 +370,76 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "capture status");
   const bool capturing = cap != cudaStreamCaptureStatusNone;
   const int jmax = ctx->batch_jmax;
-  // layout: [BatchState][done counters][phase table][instance workspaces]
-  Plan probe = build_plan(inst, count, jmax, ctx->batch_first_unit, nullptr);
-  const size_t nph = probe.phases.size();
-  const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) +
-                      up256(nph * (sizeof(BPhase) + sizeof(int64_t)));
-  if (capturing && ctx->ws_bytes < head + probe.ws_bytes) {
-    ctx->last_error = "lre_batch_run under stream capture: run the same batch once uncaptured first";
-    return LRE_ERR_UNSUPPORTED;
-  }
-  if ((st = ensure_workspace(ctx, head + probe.ws_bytes)) != LRE_OK) return st;
-  char *w = static_cast<char *>(ctx->ws);
-  BatchState *bs = reinterpret_cast<BatchState *>(w);
-  unsigned *done = reinterpret_cast<unsigned *>(w + up256(sizeof(BatchState)));
-  BPhase *dph = reinterpret_cast<BPhase *>(w + up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)));
-  Plan plan = build_plan(inst, count, jmax, ctx->batch_first_unit, w + head);
-  for (auto &b : plan.phases) b.g.status = ctx->d_status;
-  // The pass table (phases, then their first units) lives in a device buffer
-  // per distinct table (kept until lre_destroy), so a captured launch reads a
-  // table no later call rewrites; under capture the table must already exist
-  // (no allocation, no host copy).
-  std::vector<char> tab(nph * (sizeof(BPhase) + sizeof(int64_t)));
-  std::copy(reinterpret_cast<const char *>(plan.phases.data()),
-            reinterpret_cast<const char *>(plan.phases.data()) + nph * sizeof(BPhase), tab.data());
-  for (size_t k = 0; k < nph; ++k)
-    reinterpret_cast<int64_t *>(tab.data() + nph * sizeof(BPhase))[k] = plan.phases[k].unit_begin;
-  const char *bytes = tab.data();
-  const size_t tbytes = tab.size();
-  const BPhase *table = nullptr;
+  // A plan depends only on the descriptors and the schedule: an earlier call
+  // with the same ones left its pass table in a device buffer (kept until
+  // lre_destroy), so repeated and captured launches skip the host-side plan.
+  std::vector<char> key(sizeof(lre_instance) * (size_t)count + 2 * sizeof(int));
+  std::copy(reinterpret_cast<const char *>(inst), reinterpret_cast<const char *>(inst + count), key.begin());
+  const int sched[2] = {jmax, ctx->batch_first_unit};
+  std::copy(reinterpret_cast<const char *>(sched), reinterpret_cast<const char *>(sched + 2),
+            key.begin() + sizeof(lre_instance) * (size_t)count);
+  const lre_batch_entry *hit = nullptr;
   for (const auto &en : ctx->batch_cache)
-    if (en.ws == ctx->ws && en.key.size() == tbytes && std::equal(en.key.begin(), en.key.end(), bytes)) {
-      table = static_cast<const BPhase *>(en.table);
+    if (en.ws == ctx->ws && en.key == key) {
+      hit = &en;
       break;
     }
-  cudaError_t e = cudaSuccess;
-  if (!table) {
+  lre_batch_entry local;  // the plan of this call when it is not cached
+  if (!hit) {
     if (capturing) {
       ctx->last_error = "lre_batch_run under stream capture: run the same batch once uncaptured first";
       return LRE_ERR_UNSUPPORTED;
     }
-    constexpr size_t kMaxTables = 64;
+    // layout: [BatchState][done counters][phase table][instance workspaces]
+    Plan probe = build_plan(inst, count, jmax, ctx->batch_first_unit, nullptr);
+    const size_t nph = probe.phases.size();
+    const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) +
+                        up256(nph * (sizeof(BPhase) + sizeof(int64_t)));
+    if ((st = ensure_workspace(ctx, head + probe.ws_bytes)) != LRE_OK) return st;
+    char *w = static_cast<char *>(ctx->ws);
+    Plan plan = build_plan(inst, count, jmax, ctx->batch_first_unit, w + head);
+    for (auto &b : plan.phases) b.g.status = ctx->d_status;
+    std::vector<char> tab(nph * (sizeof(BPhase) + sizeof(int64_t)));
+    std::copy(reinterpret_cast<const char *>(plan.phases.data()),
+              reinterpret_cast<const char *>(plan.phases.data()) + nph * sizeof(BPhase), tab.data());
+    bool any_block = false;
+    for (size_t k = 0; k < nph; ++k) {
+      reinterpret_cast<int64_t *>(tab.data() + nph * sizeof(BPhase))[k] = plan.phases[k].unit_begin;
+      any_block = any_block || plan.phases[k].code >= C_ASM6;
+    }
+    local.key = std::move(key);
+    local.ws = ctx->ws;
+    local.nph = nph;
+    local.head = head;
+    local.ws_bytes = probe.ws_bytes;
+    local.total_units = plan.total_units;
+    local.tile_bytes = any_block ? ASM_TILE_SMEM : 0;
+    constexpr size_t kMaxPlans = 64;
+    cudaError_t e = cudaSuccess;
     void *t = nullptr;
-    if (ctx->batch_cache.size() < kMaxTables && cudaMalloc(&t, tbytes) == cudaSuccess) {
-      lre_batch_entry en;
-      en.key.assign(bytes, bytes + tbytes);
-      en.table = t;
-      en.ws = ctx->ws;
-      ctx->batch_cache.push_back(std::move(en));
-      // pageable source: staged before the call returns
-      e = cudaMemcpyAsync(t, ctx->batch_cache.back().key.data(), tbytes, cudaMemcpyHostToDevice, s);
-      table = static_cast<const BPhase *>(t);
+    if (ctx->batch_cache.size() < kMaxPlans && cudaMalloc(&t, tab.size()) == cudaSuccess) {
+      local.table = t;
+      e = cudaMemcpyAsync(t, tab.data(), tab.size(), cudaMemcpyHostToDevice, s);  // pageable: staged now
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // tab dies with this call
+      ctx->batch_cache.push_back(local);
+      hit = &ctx->batch_cache.back();
     } else {
       cudaGetLastError();
-      e = cudaMemcpyAsync(dph, bytes, tbytes, cudaMemcpyHostToDevice, s);
-      table = dph;
+      // no room to keep it: the table goes into this call's workspace
+      char *dph = w + up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned));
+      e = cudaMemcpyAsync(dph, tab.data(), tab.size(), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      local.table = dph;
+      hit = &local;
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch plan upload");
   }
-  e = cudaMemsetAsync(w, 0, up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)), s);
+  const size_t nph = hit->nph;
+  char *w = static_cast<char *>(ctx->ws);
+  BatchState *bs = reinterpret_cast<BatchState *>(w);
+  unsigned *done = reinterpret_cast<unsigned *>(w + up256(sizeof(BatchState)));
+  const BPhase *table = static_cast<const BPhase *>(hit->table);
+  cudaError_t e = cudaMemsetAsync(w, 0, up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch state reset");
   int &occ = ctx->batch_occupancy[jmax >= 3 ? 1 : 0];  // queried once, outside any capture
   if (occ == 0) {
@@ -444,17 +456,16 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   const int per_sm = std::max(1, std::min(occ, ctx->batch_ctas_per_sm));
   const int grid = ctx->num_sms * per_sm;  // every CTA resident: waits always resolve
   const int64_t *starts = reinterpret_cast<const int64_t *>(table + nph);
-  bool any_block = false;
-  for (const auto &b : plan.phases) any_block = any_block || b.code >= C_ASM6;
-  const int tile_bytes = any_block ? ASM_TILE_SMEM : 0;
+  const int tile_bytes = hit->tile_bytes;
+  const int64_t total_units = hit->total_units;
   const size_t smem = tile_bytes + (nph <= (size_t)BATCH_SMEM_PHASES ? nph * sizeof(int64_t) : 0);
   {
     Launch L(ctx, "batch_kernel", s);
     if (jmax >= 3)
-      batch_kernel<3><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, tile_bytes,
+      batch_kernel<3><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, total_units, tile_bytes,
                                               ctx->d_status);
     else
-      batch_kernel<2><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, plan.total_units, tile_bytes,
+      batch_kernel<2><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, total_units, tile_bytes,
                                               ctx->d_status);
   }
   e = cudaGetLastError();

@@ -18,13 +18,17 @@ struct lre_prof_entry {
   cudaEvent_t start, stop;
 };
 
-// One batched pass table kept on the device (lre_batch_run): the table's
-// bytes, its device copy, and the workspace it points into.  Entries are
+// One batched plan kept on the device (lre_batch_run), keyed by the
+// instance descriptors and the schedule: the pass table's device copy, the
+// workspace it points into, and what a launch over it needs.  Entries are
 // immutable, so a CUDA graph that captured a launch over one stays valid.
 struct lre_batch_entry {
-  std::vector<char> key;
-  void *table = nullptr;
+  std::vector<char> key;      // descriptors + schedule
+  void *table = nullptr;      // device: phases, then their first units
   void *ws = nullptr;
+  size_t nph = 0, head = 0, ws_bytes = 0;
+  int64_t total_units = 0;
+  int tile_bytes = 0;
 };
 
 struct lre_ctx {
