@@ -147,7 +147,8 @@ lre_status launch(lre_ctx *ctx, const CUtensorMap &map, const CUtensorMap &map_h
   const int64_t cap = (int64_t)ctx->num_sms * (smem <= 110 * 1024 ? 2 : 1);
   if (grid > cap) grid = cap;
   k<<<(unsigned)grid, TMA_WARPS * 32, smem, s>>>(map, map_hi, P);
-  return LRE_OK;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "TMA fold pass launch");
 }
 
 }  // namespace
@@ -184,13 +185,13 @@ lre_status passes::tma_pass(lre_ctx *ctx, const GenParams &P, int J, int in_t, i
     if (!encode_tensor_map(&map_hi, CU_TENSOR_MAP_DATA_TYPE_UINT8, static_cast<const char *>(P.in) + elems * 2, 5,
                            dims, strides, box))
       return LRE_ERR_UNSUPPORTED;
-    Launch L(ctx, "fold_pass", s);
+    Launch L(ctx, "fold_tma", s);
     return launch<3, int32_t, M_STORE, true>(ctx, map, map_hi, P, s);
   }
   strides_of(4, strides);
   if (!encode_tensor_map_i32(&map, P.in, 5, dims, strides, box)) return LRE_ERR_UNSUPPORTED;
   map_hi = map;
-  Launch L(ctx, mode == M_STORE ? "fold_pass" : "fold_final", s);
+  Launch L(ctx, "fold_tma", s);
   const bool i64 = acc_t == T_I64;
 #define LRE_TMA_CASE(JJ)                                                                                  \
   if (J == JJ) {                                                                                          \

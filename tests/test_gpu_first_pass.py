@@ -47,24 +47,25 @@ def test_fused_second_pass_equals_unfused(n, dt):
     """The first pass fused with the second through L2 gives the same exact
     integer parity sums as the two passes run separately."""
     torch = need_gpu()
-    lre, ctx = ctx_and_lre()
-    L = lre.load()
-    f = L.lre_debug_set_first_pass
-    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
-    f.restype = ctypes.c_int
-    try:
-        from synth import gen
-        c = torch.empty((3 ** n, 2 ** n), dtype=torch.int16 if dt == np.int16 else torch.int32, device="cuda")
-        gen.gen_ghz(n, 0.05, 1000, 77 + n, c)
-        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_FWHT)  # both sides on the ALU kernels
-        res = []
-        for variant in (1, 2):
+    from synth import gen
+    c = torch.empty((3 ** n, 2 ** n), dtype=torch.int16 if dt == np.int16 else torch.int32, device="cuda")
+    gen.gen_ghz(n, 0.05, 1000, 77 + n, c)
+    res = []
+    for variant, kernel in ((2, "fold_first9_fused"), (1, "fold_first6")):
+        lre, ctx = ctx_and_lre()  # one context per variant: no shared workspace
+        try:
+            f = lre.load().lre_debug_set_first_pass
+            f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            f.restype = ctypes.c_int
+            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_FWHT)  # both sides on the ALU kernels
             assert f(ctx, variant) == 0
-            S = torch.empty(4 ** n, dtype=torch.int64, device="cuda")
+            S = torch.full((4 ** n,), -1, dtype=torch.int64, device="cuda")
+            lre.lre_profile(ctx, True)
             lre.lre_parity_sums(ctx, c, n, S, row_total_bound=1000)
             lre.lre_sync(ctx)
+            assert kernel in {k for k, _ in lre.lre_profile_records(ctx)}
             res.append(S)
-        assert torch.equal(res[0], res[1])
-        assert int(res[1][0]) == 1000 * 3 ** n
-    finally:
-        lre.lre_destroy(ctx)
+        finally:
+            lre.lre_destroy(ctx)
+    assert torch.equal(res[0], res[1])
+    assert int(res[1][0]) == 1000 * 3 ** n

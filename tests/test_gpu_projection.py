@@ -144,8 +144,8 @@ def test_partial_equals_full_path(n):
         outs, eigs = [], []
         for mode in (0, 1):
             _mode(lre, ctx, mode)
-            out = torch.empty_like(mu)
-            er = torch.empty(2 ** n, dtype=torch.float64, device="cuda")
+            out = torch.full_like(mu, float("nan"))  # nothing left from the other mode
+            er = torch.full((2 ** n,), float("nan"), dtype=torch.float64, device="cuda")
             lre.lre_project(ctx, mu, n, out, eig_rho=er)
             lre.lre_sync(ctx)
             outs.append(out.cpu().numpy())

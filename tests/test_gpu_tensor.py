@@ -27,28 +27,34 @@ def _set_variant(lre, ctx, biased):
     assert f(ctx, biased) == 0
 
 
+def _sums_by_path(torch, c, n, bound, biased=0):
+    """Parity sums through the tensor-core path, then the FWHT path, each in
+    a context of its own (no workspace shared between the two)."""
+    res = []
+    for tensor in (True, False):
+        lre, ctx = ctx_and_lre()
+        try:
+            _set_variant(lre, ctx, biased)
+            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if tensor else lre.LRE_FOLD_FWHT)
+            S = torch.full((4 ** n,), -1, dtype=torch.int64, device="cuda")
+            lre.lre_profile(ctx, True)
+            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=bound)
+            lre.lre_sync(ctx)
+            names = [k for k, _ in lre.lre_profile_records(ctx)]
+            assert ("fold_first6_mma" in names) == tensor, names
+            res.append(S)
+        finally:
+            lre.lre_destroy(ctx)
+    return res
+
+
 @pytest.mark.parametrize("biased", [0, 1])
 @pytest.mark.parametrize("n", [7, 8, 10, 11])
 def test_tensor_parity_sums_equal_fwht(n, biased):
     torch = need_gpu()
-    lre, ctx = ctx_and_lre()
-    try:
-        _set_variant(lre, ctx, biased)
-        c = _counts(torch, n, 1000, 90 + n)
-        res = []
-        for path in (lre.LRE_FOLD_FWHT, lre.LRE_FOLD_TENSOR):
-            lre.lre_set_fold_path(ctx, path)
-            S = torch.empty(4 ** n, dtype=torch.int64, device="cuda")
-            lre.lre_profile(ctx, True)
-            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=1000)
-            lre.lre_sync(ctx)
-            names = [k for k, _ in lre.lre_profile_records(ctx)]
-            lre.lre_profile(ctx, False)
-            assert ("fold_first6_mma" in names) == (path == lre.LRE_FOLD_TENSOR), names
-            res.append(S)
-        assert torch.equal(res[0], res[1])
-    finally:
-        lre.lre_destroy(ctx)
+    c = _counts(torch, n, 1000, 90 + n)
+    res = _sums_by_path(torch, c, n, 1000, biased)
+    assert torch.equal(res[0], res[1])
 
 
 @pytest.mark.parametrize("biased,top", [(0, 2047), (1, 1023)])
@@ -83,18 +89,52 @@ def test_tensor_first_pass_n12_equals_fwht():
     """Headline-shaped case: many tiles per CTA, both level-B warp pairs and
     every ring slot in use."""
     torch = need_gpu()
+    n = 12
+    c = _counts(torch, n, 1000, 1234)
+    res = _sums_by_path(torch, c, n, 1000)
+    assert torch.equal(res[0], res[1])
+    assert int(res[0][0]) == 1000 * 3 ** n
+
+
+def _bound_rows(torch, n, shots, seed):
+    """GHZ + noise counts with two whole tile rows (729 consecutive bases)
+    driven to the partial-sum bound: every shot in outcome 0 (all partials
+    +3^k N) and every shot in the all-ones outcome (sign by parity)."""
+    c = _counts(torch, n, shots, seed)
+    c[0:729] = 0
+    c[0:729, 0] = shots
+    c[729:1458] = 0
+    c[729:1458, 2 ** n - 1] = shots
+    return c
+
+
+# shots per basis around the partial-sum sizes the split planes meet: 729 x 44
+# fits int16 and 729 x 45 does not (the all-identity partial), 2047 is the
+# largest raw count (729 x 2047 < 2^21 in the 24-bit planes).
+@pytest.mark.parametrize("shots", [44, 45, 1000, 2047])
+def test_split_planes_at_bound_partials_equal_fwht(shots):
+    torch = need_gpu()
+    n = 10
+    c = _bound_rows(torch, n, shots, 500 + shots)
+    res = _sums_by_path(torch, c, n, shots)
+    assert torch.equal(res[0], res[1])
+    assert int(res[0][0]) == shots * 3 ** n
+
+
+def test_split_plane_theta_matches_oracle():
+    """theta through the tensor first pass and the split planes, with whole
+    tile rows at the partial-sum bound, against the oracle."""
+    torch = need_gpu()
     lre, ctx = ctx_and_lre()
     try:
-        n = 12
-        c = _counts(torch, n, 1000, 1234)
-        res = []
-        for path in (lre.LRE_FOLD_FWHT, lre.LRE_FOLD_TENSOR):
-            lre.lre_set_fold_path(ctx, path)
-            S = torch.empty(4 ** n, dtype=torch.int64, device="cuda")
-            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=1000)
-            lre.lre_sync(ctx)
-            res.append(S)
-        assert torch.equal(res[0], res[1])
-        assert int(res[1][0]) == 1000 * 3 ** n
+        n, shots = 10, 45
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+        c = _bound_rows(torch, n, shots, 77)
+        theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
+        lre.lre_estimate(ctx, c, shots, n, theta)
+        lre.lre_sync(ctx)
+        np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(c.cpu().numpy(), shots, n))
     finally:
         lre.lre_destroy(ctx)
+
+
