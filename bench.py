@@ -549,7 +549,7 @@ def run_batched(args):
         "config": {"workload": "256 instances, n ~ U{3..9}, random-rank (1..4) Ginibre mixtures, "
                                "shots/basis log-uniform 500..10000, int32 counts",
                    "bases": bases, "count_bytes": count_bytes,
-                   "schedule": {"tuned_ms": round(tuned_ms, 4)}},
+                   "schedule": dict(lre.lre_batch_schedule(ctx), tuned_ms=round(tuned_ms, 4))},
         "batched": {"ms": round(ms_batch, 4), "launches_per_step": batch_launches,
                     "count_gbs": round(count_bytes / (ms_batch / 1e3) / 1e9, 1),
                     "frac_hbm_counts": round(count_bytes / (ms_batch / 1e3) / 1e9 / peak, 4)},

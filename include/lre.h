@@ -212,11 +212,18 @@ lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre
 
 /* Autotuner for lre_batch_run: times the candidate schedules (qubits per
  * fold pass 2 or 3; 1 or 2 resident CTAs per SM; 256 or 1024 items per work
- * unit of the count-reading first passes) on this batch, keeps the
+ * unit of the count-reading first passes; 256, 1024 or 4096 items per work
+ * unit of the other fold and assembly passes) on this batch, keeps the
  * fastest in the context for later lre_batch_run calls, and returns its time
  * per launch in *best_ms (may be NULL).  Synchronises `stream`. */
 lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream,
                           float *best_ms);
+
+/* The batched schedule this context uses (set by lre_batch_tune, or the
+ * defaults): qubits per fold pass (jmax), resident CTAs per SM, items per
+ * work unit of the count-reading first passes and of the other passes.  Any
+ * output pointer may be NULL.  Host only; LRE_ERR_INVALID_ARG for ctx NULL. */
+lre_status lre_batch_schedule(const lre_ctx *ctx, int *jmax, int *ctas_per_sm, int *first_unit, int *unit);
 
 /* First fold pass of step (i) (the first six qubits) on later calls of this
  * context:

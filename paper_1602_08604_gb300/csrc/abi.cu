@@ -456,6 +456,16 @@ extern "C" lre_status lre_batch_tune(lre_ctx *ctx, const lre_instance *descs, in
   return lre::batch_tune(ctx, descs, count, reinterpret_cast<cudaStream_t>(stream), best_ms);
 }
 
+extern "C" lre_status lre_batch_schedule(const lre_ctx *ctx, int *jmax, int *ctas_per_sm, int *first_unit,
+                                         int *unit) {
+  if (!ctx) return LRE_ERR_INVALID_ARG;
+  if (jmax) *jmax = ctx->batch_jmax;
+  if (ctas_per_sm) *ctas_per_sm = ctx->batch_ctas_per_sm;
+  if (first_unit) *first_unit = ctx->batch_first_unit;
+  if (unit) *unit = ctx->batch_unit;
+  return LRE_OK;
+}
+
 extern "C" lre_status lre_set_fold_path(lre_ctx *ctx, int path) {
   if (!ctx || (path != LRE_FOLD_FWHT && path != LRE_FOLD_TENSOR)) return LRE_ERR_INVALID_ARG;
   ctx->fold_path = path;

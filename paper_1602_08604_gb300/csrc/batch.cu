@@ -205,7 +205,7 @@ struct Plan {
 
 // Per-instance pass lists, workspace offsets relative to `base`, then the
 // pass-major global order.
-Plan build_plan(const lre_instance *inst, int count, int jmax, int first_unit, char *base) {
+Plan build_plan(const lre_instance *inst, int count, int jmax, int first_unit, int unit, char *base) {
   std::vector<std::vector<BPhase>> per(count);
   size_t off = 0;
   for (int i = 0; i < count; ++i) {
@@ -275,9 +275,10 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, int first_unit, c
         g.up3[kk] = kk <= n ? ipow(3, n - kk) : 0;
       }
       b.items = g.items;
-      // count-reading first passes do the most work per item; larger units
-      // there amortise the claim, wait and publish of a unit
-      b.per_unit = k == 0 ? first_unit : 256;
+      // a unit's claim, dependency wait and publish cost about as much as
+      // moving a few hundred items' data: larger units amortise them (the
+      // count-reading first passes and the rest are tuned separately)
+      b.per_unit = k == 0 ? first_unit : unit;
       per[i].push_back(b);
       in = g.out;
     }
@@ -317,7 +318,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, int first_unit, c
         a.items = (1ll << (2 * (n - tt - J))) << (2 * tt);
         a.scale = LastScale{sc.sh, sc.sl};
         b.items = a.items;
-        b.per_unit = 256;
+        b.per_unit = unit;
         per[i].push_back(b);
         ain = a.out;
         tt += J;
@@ -373,10 +374,10 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   // A plan depends only on the descriptors and the schedule: an earlier call
   // with the same ones left its pass table in a device buffer (kept until
   // lre_destroy), so repeated and captured launches skip the host-side plan.
-  std::vector<char> key(sizeof(lre_instance) * (size_t)count + 2 * sizeof(int));
+  const int sched[3] = {jmax, ctx->batch_first_unit, ctx->batch_unit};
+  std::vector<char> key(sizeof(lre_instance) * (size_t)count + sizeof(sched));
   std::copy(reinterpret_cast<const char *>(inst), reinterpret_cast<const char *>(inst + count), key.begin());
-  const int sched[2] = {jmax, ctx->batch_first_unit};
-  std::copy(reinterpret_cast<const char *>(sched), reinterpret_cast<const char *>(sched + 2),
+  std::copy(reinterpret_cast<const char *>(sched), reinterpret_cast<const char *>(sched + 3),
             key.begin() + sizeof(lre_instance) * (size_t)count);
   const lre_batch_entry *hit = nullptr;
   for (const auto &en : ctx->batch_cache)
@@ -391,13 +392,13 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
       return LRE_ERR_UNSUPPORTED;
     }
     // layout: [BatchState][done counters][phase table][instance workspaces]
-    Plan probe = build_plan(inst, count, jmax, ctx->batch_first_unit, nullptr);
+    Plan probe = build_plan(inst, count, jmax, ctx->batch_first_unit, ctx->batch_unit, nullptr);
     const size_t nph = probe.phases.size();
     const size_t head = up256(sizeof(BatchState)) + up256(nph * sizeof(unsigned)) +
                         up256(nph * (sizeof(BPhase) + sizeof(int64_t)));
     if ((st = ensure_workspace(ctx, head + probe.ws_bytes)) != LRE_OK) return st;
     char *w = static_cast<char *>(ctx->ws);
-    Plan plan = build_plan(inst, count, jmax, ctx->batch_first_unit, w + head);
+    Plan plan = build_plan(inst, count, jmax, ctx->batch_first_unit, ctx->batch_unit, w + head);
     for (auto &b : plan.phases) b.g.status = ctx->d_status;
     std::vector<char> tab(nph * (sizeof(BPhase) + sizeof(int64_t)));
     std::copy(reinterpret_cast<const char *>(plan.phases.data()),
@@ -477,20 +478,23 @@ lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStr
   if (st != LRE_OK) return st;
   const int cand_j[2] = {2, 3};
   const int cand_occ[2] = {1, 2};       // resident CTAs per SM (the kernel fits at most two)
-  const int cand_unit[2] = {256, 1024};  // items per unit of the count-reading first passes
+  const int cand_first[2] = {256, 1024};  // items per unit of the count-reading first passes
+  const int cand_unit[3] = {256, 1024, 4096};  // items per unit of the other fold and assembly passes
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     return LRE_ERR_CUDA;
   }
   float best = 1e30f;
-  int bj = ctx->batch_jmax, bo = ctx->batch_ctas_per_sm, bu = ctx->batch_first_unit;
+  int bj = ctx->batch_jmax, bo = ctx->batch_ctas_per_sm, bf = ctx->batch_first_unit, bu = ctx->batch_unit;
   for (int j : cand_j) {
     for (int o : cand_occ) {
-      for (int u : cand_unit) {
+      for (int cand = 0; cand < 6; ++cand) {
+        const int f = cand_first[cand & 1], u = cand_unit[cand >> 1];
         ctx->batch_jmax = j;
         ctx->batch_ctas_per_sm = o;
-        ctx->batch_first_unit = u;
+        ctx->batch_first_unit = f;
+        ctx->batch_unit = u;
         if ((st = batch_run(ctx, inst, count, s)) != LRE_OK) break;  // warm-up
         cudaEventRecord(e0, s);
         for (int rep = 0; rep < 3 && st == LRE_OK; ++rep) st = batch_run(ctx, inst, count, s);
@@ -504,6 +508,7 @@ lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStr
           best = ms;
           bj = j;
           bo = o;
+          bf = f;
           bu = u;
         }
       }
@@ -515,7 +520,8 @@ lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStr
   cudaEventDestroy(e1);
   ctx->batch_jmax = bj;
   ctx->batch_ctas_per_sm = bo;
-  ctx->batch_first_unit = bu;
+  ctx->batch_first_unit = bf;
+  ctx->batch_unit = bu;
   if (best_ms) *best_ms = best;
   return st;
 }

@@ -57,6 +57,7 @@ struct lre_ctx {
   int batch_jmax = 3;         // batched schedule: qubits per fold pass
   int batch_ctas_per_sm = 2;  // batched schedule: resident CTAs per SM
   int batch_first_unit = 1024;  // batched schedule: items per unit of the count-reading first passes
+  int batch_unit = 256;         // batched schedule: items per unit of the other fold and assembly passes
   int batch_occupancy[2] = {0, 0};  // most resident CTAs per SM of batch_kernel<2>, <3>
   std::vector<lre_batch_entry> batch_cache;  // device pass tables of earlier batched calls
   size_t host_chunk_bytes = 256ull << 20; // host-input streaming: bytes of input per chunk

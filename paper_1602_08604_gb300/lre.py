@@ -55,6 +55,7 @@ SIGNATURES = [
     ("lre_estimate_host", _i, [_p, _p, _i, _i64, _i, _p, _p, _p]),
     ("lre_batch_run", _i, [_p, _p, _i, _p]),
     ("lre_batch_tune", _i, [_p, _p, _i, _p, ctypes.POINTER(ctypes.c_float)]),
+    ("lre_batch_schedule", _i, [_p] + [ctypes.POINTER(_i)] * 4),
     ("lre_set_fold_path", _i, [_p, _i]),
     ("lre_sync", _i, [_p, _p]),
     ("lre_status_string", ctypes.c_char_p, [_i]),
@@ -206,6 +207,13 @@ def lre_batch_tune(ctx, items, stream=None):
     _check(load().lre_batch_tune(ctx, ctypes.cast(arr, ctypes.c_void_p), len(arr), _stream(stream),
                                  ctypes.byref(ms)), ctx)
     return ms.value
+
+
+def lre_batch_schedule(ctx):
+    """The context's batched schedule as a dict (jmax, ctas_per_sm, first_unit, unit)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().lre_batch_schedule(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return dict(zip(("jmax", "ctas_per_sm", "first_unit", "unit"), (x.value for x in v)))
 
 
 def lre_set_fold_path(ctx, path):

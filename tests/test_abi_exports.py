@@ -62,3 +62,6 @@ def test_arguments_rejected_before_any_device_work(lib):
     assert lib.lre_profile_count(None) == 0
     n = ctypes.c_size_t()
     assert lib.lre_workspace_size(None, 4, 0, 0, ctypes.byref(n)) == 1
+    j = ctypes.c_int(-1)
+    assert lib.lre_batch_schedule(None, ctypes.byref(j), None, None, None) == 1
+    assert j.value == -1

@@ -65,6 +65,9 @@ def test_batch_tune_then_run(batch):
     lre, ctx = ctx_and_lre()
     try:
         ms = lre.lre_batch_tune(ctx, items)
+        sch = lre.lre_batch_schedule(ctx)
+        assert sch["jmax"] in (2, 3) and sch["ctas_per_sm"] in (1, 2)
+        assert sch["first_unit"] in (256, 1024) and sch["unit"] in (256, 1024, 4096)
         assert ms > 0
         for _, _, _, theta, rho in items:
             theta.fill_(float("nan"))
