@@ -96,6 +96,111 @@ __device__ __forceinline__ void run_item(const BPhase &P, int64_t item) {
   }
 }
 
+// Count-reading first fold pass (C == 1, store mode) with its rows staged
+// through shared memory: a thread's items (first, first + 256, ...) read NA
+// rows of 2^J counts each, and a thread running the register form has room
+// for about two row loads in flight next to its 4^J accumulators -- a DRAM
+// round trip per row or two.  Here each thread keeps STAGE_ROWS rows in
+// flight as cp.async copies into its own shared-memory slots (no registers
+// held), one commit group per row, the pipeline running across its items.
+// Slot layout [slot][16-byte half][thread]: a warp's 16-byte reads of one
+// half are contiguous.
+constexpr int STAGE_ROWS = 8;
+
+template <int J, typename InT>
+__device__ __forceinline__ void first_pass_staged(const BPhase &P, int64_t first, int count, unsigned char *stage) {
+  constexpr int NA = J == 2 ? 9 : 27;
+  constexpr int NO = 1 << J;
+  constexpr int NP = 1 << (2 * J);
+  constexpr int ROWB = NO * (int)sizeof(InT);  // 8, 16 or 32 bytes
+  constexpr int HALVES = ROWB > 16 ? 2 : 1;
+  constexpr int PIECE = ROWB > 16 ? 16 : ROWB;
+  const GenParams &g = P.g;
+  const InT *in = static_cast<const InT *>(g.in);
+  const int t = threadIdx.x;
+  const int total = count * NA;                   // rows of this thread, in item order
+  // issue cursor: row `nf` of the stream, item `ni`, basis digit `nal`, and the
+  // item's first row (one division per item, not per row)
+  int nf = 0, ni = 0, nal = 0;
+  const InT *nrow = nullptr;
+  auto item_row0 = [&](int it) {
+    const int64_t item = first + (int64_t)it * 256;
+    const int64_t ah = item / g.n_oh, oh = item - ah * g.n_oh;
+    return in + ((ah * NA) << g.r) + oh * NO;
+  };
+  if (total > 0) nrow = item_row0(0);
+  auto issue = [&]() {  // the next row of the stream into its slot, then one commit group
+    if (nf < total) {
+      const InT *src = nrow + ((int64_t)nal << g.r);
+#pragma unroll
+      for (int h = 0; h < HALVES; ++h) {
+        unsigned char *dst = stage + (((nf % STAGE_ROWS) * HALVES + h) * 256 + t) * PIECE;
+        if constexpr (PIECE == 16)
+          sm103::cp_async16(dst, reinterpret_cast<const unsigned char *>(src) + h * 16);
+        else
+          sm103::cp_async8(dst, src);
+      }
+      if (++nal == NA) {
+        nal = 0;
+        if (++ni < count) nrow = item_row0(ni);
+      }
+    }
+    ++nf;
+    sm103::cp_async_commit();  // empty past the end: keeps one group per row
+  };
+  for (int f = 0; f < STAGE_ROWS; ++f) issue();
+  for (int it = 0; it < count; ++it) {
+    int32_t acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = 0;
+#pragma unroll
+    for (int al = 0; al < NA; ++al) {
+      const int f = it * NA + al;
+      sm103::cp_async_wait<STAGE_ROWS - 1>();  // row f has landed
+      uint32_t w[ROWB / 4 > 0 ? ROWB / 4 : 1];
+#pragma unroll
+      for (int h = 0; h < HALVES; ++h) {
+        const unsigned char *src = stage + (((f % STAGE_ROWS) * HALVES + h) * 256 + t) * PIECE;
+        if constexpr (PIECE == 16) {
+          const uint4 q = *reinterpret_cast<const uint4 *>(src);
+          w[h * 4 + 0] = q.x; w[h * 4 + 1] = q.y; w[h * 4 + 2] = q.z; w[h * 4 + 3] = q.w;
+        } else {
+          const uint2 q = *reinterpret_cast<const uint2 *>(src);
+          w[0] = q.x; w[1] = q.y;
+        }
+      }
+      issue();  // row f + STAGE_ROWS, into the slot just read
+      int32_t v[NO];
+#pragma unroll
+      for (int k = 0; k < NO; ++k) {
+        if constexpr (sizeof(InT) == 2)
+          v[k] = (int32_t)(int16_t)(uint16_t)(w[k >> 1] >> (16 * (k & 1)));
+        else
+          v[k] = (int32_t)w[k];
+      }
+      wht<J>(v);
+#pragma unroll
+      for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
+    }
+    // C == 1: the item's 4^J partials are contiguous; 16-byte stores (a
+    // thread's scalar stores would put 4 bytes into 32 separate sectors per
+    // warp instruction)
+    int4 *o = reinterpret_cast<int4 *>(static_cast<int32_t *>(g.out) + (first + (int64_t)it * 256) * NP);
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) o[q] = make_int4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+  }
+  sm103::cp_async_wait<0>();
+}
+
+// Bytes of shared staging the staged first pass needs.
+constexpr int STAGE_BYTES = STAGE_ROWS * 256 * 32;
+static_assert(STAGE_BYTES <= ASM_TILE_SMEM, "the staging fits the assembly tile");
+
+// Codes of the count-reading first passes (store mode, J >= 2) that run staged.
+__host__ __device__ constexpr bool staged_code(int code) {
+  return code == C_FOLD + 12 || code == C_FOLD + 14 || code == C_FOLD + 20 || code == C_FOLD + 22;
+}
+
 constexpr int BATCH_SMEM_PHASES = 4096;  // phase starts cached in shared memory up to this many
 
 // Last phase with unit_begin <= u (binary search over the phase starts).
@@ -177,6 +282,24 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict_
         asm_low6_block<NumI64, true>(in, P.a.out, blk, tile, P.a.scale);
       else
         asm_low6_block<NumI64, false>(in, P.a.out, blk, tile, P.a.scale);
+    } else if (staged_code(P.code) && tile_bytes >= STAGE_BYTES &&
+               ((reinterpret_cast<uintptr_t>(P.g.in) | reinterpret_cast<uintptr_t>(P.g.out)) & 15) == 0) {
+      const int64_t first = (s_unit - P.unit_begin) * P.per_unit + threadIdx.x;
+      const int64_t left = P.items > first ? (P.items - first + 255) / 256 : 0;
+      const int count = (int)(left < P.per_unit / 256 ? left : P.per_unit / 256);
+      unsigned char *stage = bsmem;
+      if (count > 0) {
+        switch (P.code) {
+          case C_FOLD + 12: first_pass_staged<2, int16_t>(P, first, count, stage); break;
+          case C_FOLD + 14: first_pass_staged<2, int32_t>(P, first, count, stage); break;
+          case C_FOLD + 20:
+            if constexpr (JMAX >= 3) first_pass_staged<3, int16_t>(P, first, count, stage);
+            break;
+          default:
+            if constexpr (JMAX >= 3) first_pass_staged<3, int32_t>(P, first, count, stage);
+            break;
+        }
+      }
     } else {
       const int64_t first = (s_unit - P.unit_begin) * P.per_unit + threadIdx.x;
       for (int k = 0; k < P.per_unit; k += 256) {
@@ -406,7 +529,7 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
     bool any_block = false;
     for (size_t k = 0; k < nph; ++k) {
       reinterpret_cast<int64_t *>(tab.data() + nph * sizeof(BPhase))[k] = plan.phases[k].unit_begin;
-      any_block = any_block || plan.phases[k].code >= C_ASM6;
+      any_block = any_block || plan.phases[k].code >= C_ASM6 || staged_code(plan.phases[k].code);
     }
     local.key = std::move(key);
     local.ws = ctx->ws;
