@@ -7,14 +7,17 @@
 // the exact integers T = S 3^(n-k) on) and the exact-integer assembly passes
 // of step (ii) (Eq. 4).  All passes of all instances form one list ordered
 // pass-major (the first pass of every instance, then the second, ...), cut
-// into work units of 256 items.  Each CTA of the persistent grid claims
-// units from a device counter; a unit first waits (bounded by time) until
+// into work units of a tuned number of items.  Each CTA of the persistent
+// grid claims units from a device counter; a unit first waits (bounded by
+// time) until
 // every unit of its instance's previous pass has finished, then runs.  The
 // pass-major order means a CTA only ever waits on units claimed before its
 // own, so with every CTA resident the launch always completes.
 //
-// The "schedule" (JMAX, CTAs per SM) is picked by lre_batch_tune, which times
-// the candidates on the caller's batch and keeps the fastest in the context.
+// The "schedule" (JMAX, CTAs per SM, items per unit of the count-reading
+// first passes and of the other passes) is picked by lre_batch_tune, which
+// times the candidates on the caller's batch and keeps the fastest in the
+// context.
 #include <cuda_runtime.h>
 
 #include <algorithm>
