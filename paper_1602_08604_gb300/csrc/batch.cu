@@ -9,10 +9,9 @@
 // pass-major (the first pass of every instance, then the second, ...), cut
 // into work units of a tuned number of items.  Each CTA of the persistent
 // grid claims units from a device counter; a unit first waits (bounded by
-// time) until
-// every unit of its instance's previous pass has finished, then runs.  The
-// pass-major order means a CTA only ever waits on units claimed before its
-// own, so with every CTA resident the launch always completes.
+// time) until every unit of its instance's previous pass has finished, then
+// runs.  The pass-major order means a CTA only ever waits on units claimed
+// before its own, so with every CTA resident the launch always completes.
 //
 // The "schedule" (JMAX, CTAs per SM, items per unit of the count-reading
 // first passes and of the other passes) is picked by lre_batch_tune, which
