@@ -441,6 +441,21 @@ extern "C" lre_status lre_debug_set_mma_variant(lre_ctx *ctx, int biased) {
   return LRE_OK;
 }
 
+// Test hook: set the batched schedule directly (any of the autotuner's
+// candidates: jmax 2 or 3, 1 or 2 CTAs per SM, units that are multiples of
+// 256 items).
+extern "C" lre_status lre_debug_set_batch_schedule(lre_ctx *ctx, int jmax, int ctas_per_sm, int first_unit,
+                                                   int unit) {
+  if (!ctx || jmax < 2 || jmax > 3 || ctas_per_sm < 1 || ctas_per_sm > 2 || first_unit < 256 ||
+      first_unit % 256 != 0 || unit < 256 || unit % 256 != 0)
+    return LRE_ERR_INVALID_ARG;
+  ctx->batch_jmax = jmax;
+  ctx->batch_ctas_per_sm = ctas_per_sm;
+  ctx->batch_first_unit = first_unit;
+  ctx->batch_unit = unit;
+  return LRE_OK;
+}
+
 extern "C" lre_status lre_batch_run(lre_ctx *ctx, const lre_instance *descs, int count, lre_stream stream) {
   if (!ctx) return LRE_ERR_INVALID_ARG;
   lre_status st = set_device(ctx);

@@ -78,6 +78,32 @@ def test_batch_tune_then_run(batch):
         lre.lre_destroy(ctx)
 
 
+# the autotuner may keep any of its candidates: each must give the same
+# results (J = 2 and 3 first passes staged, int16 and int32 counts, small and
+# large units, one and two CTAs per SM)
+@pytest.mark.parametrize("sched", [(2, 1, 256, 256), (2, 2, 1024, 4096), (3, 1, 1024, 256),
+                                   (3, 2, 256, 1024), (3, 2, 1024, 4096)])
+def test_every_schedule_matches_per_instance(batch, sched):
+    import ctypes
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    try:
+        f = lre.load().lre_debug_set_batch_schedule
+        f.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 4
+        f.restype = ctypes.c_int
+        assert f(ctx, *sched) == 0
+        assert tuple(lre.lre_batch_schedule(ctx).values()) == sched
+        for _, _, _, theta, rho in items:
+            theta.fill_(float("nan"))
+            if rho is not None:
+                rho.fill_(float("nan"))
+        lre.lre_batch_run(ctx, items)
+        lre.lre_sync(ctx)
+        _check_against_single(torch, lre, ctx, items, host)
+    finally:
+        lre.lre_destroy(ctx)
+
+
 def test_batch_rejects_large_n(batch):
     torch, items, host = batch
     lre, ctx = ctx_and_lre()
