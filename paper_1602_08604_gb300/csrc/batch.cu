@@ -41,6 +41,7 @@ enum : int {
 
 struct BPhase {
   int code;
+  int inst;         // the instance the pass belongs to (host bookkeeping)
   int dep;          // index of the phase this one waits for (-1: none)
   unsigned dep_units;
   int per_unit;     // items per work unit: a multiple of 256 (each thread takes every 256th), or 1 (a
@@ -461,6 +462,7 @@ Plan build_plan(const lre_instance *inst, int count, int jmax, int first_unit, i
     for (int i = 0; i < count; ++i) {
       if (k >= per[i].size()) continue;
       BPhase b = per[i][k];
+      b.inst = i;
       b.units = (b.items + b.per_unit - 1) / b.per_unit;
       b.unit_begin = u;
       u += b.units;
@@ -652,3 +654,21 @@ lre_status batch_tune(lre_ctx *ctx, const lre_instance *inst, int count, cudaStr
 }
 
 }  // namespace lre
+
+// Test hook (host only, no device work): the pass table lre_batch_run would
+// build for these descriptors and this schedule.  Per phase, 8 int64 at
+// out + 8 k: instance, code, dep, dep_units, per_unit, unit_begin, units,
+// items (at most max_phases phases written).  Returns the number of phases,
+// or -1 when the descriptors are rejected.
+extern "C" int lre_debug_batch_plan(const lre_instance *descs, int count, int jmax, int first_unit, int unit,
+                                    int64_t *out, int max_phases) {
+  if (lre::validate(descs, count) != LRE_OK || jmax < 1 || first_unit < 256 || unit < 256) return -1;
+  const lre::Plan plan = lre::build_plan(descs, count, jmax, first_unit, unit, nullptr);
+  const int nph = (int)plan.phases.size();
+  for (int k = 0; out && k < nph && k < max_phases; ++k) {
+    const lre::BPhase &b = plan.phases[k];
+    const int64_t v[8] = {b.inst, b.code, b.dep, (int64_t)b.dep_units, b.per_unit, b.unit_begin, b.units, b.items};
+    for (int f = 0; f < 8; ++f) out[8 * k + f] = v[f];
+  }
+  return nph;
+}
