@@ -101,11 +101,13 @@ __device__ __forceinline__ void run_item(const BPhase &P, int64_t item) {
 
 // Count-reading first fold pass (C == 1, store mode) with its rows staged
 // through shared memory: a thread's items (first, first + 256, ...) read NA
-// rows of 2^J counts each, and a thread running the register form has room
-// for about two row loads in flight next to its 4^J accumulators -- a DRAM
-// round trip per row or two.  Here each thread keeps STAGE_ROWS rows in
-// flight as cp.async copies into its own shared-memory slots (no registers
-// held), one commit group per row, the pipeline running across its items.
+// rows of 2^J counts each.  Instead of the register form's few row loads
+// in flight next to its 4^J accumulators, each thread keeps STAGE_ROWS rows
+// in flight as cp.async copies into its own shared-memory slots (no
+// registers held), one commit group per row, the pipeline running across
+// its items; each item's 4^J partials, contiguous because C == 1, leave as
+// 16-byte stores (the register form's scalar stores put 4 bytes into 32
+// separate sectors per warp instruction, which is what held this pass back).
 // Slot layout [slot][16-byte half][thread]: a warp's 16-byte reads of one
 // half are contiguous.
 constexpr int STAGE_ROWS = 8;
@@ -185,9 +187,6 @@ __device__ __forceinline__ void first_pass_staged(const BPhase &P, int64_t first
 #pragma unroll
       for (int m = 0; m < NO; ++m) acc[block_pauli(al, m, J)] += v[m];
     }
-    // C == 1: the item's 4^J partials are contiguous; 16-byte stores (a
-    // thread's scalar stores would put 4 bytes into 32 separate sectors per
-    // warp instruction)
     int4 *o = reinterpret_cast<int4 *>(static_cast<int32_t *>(g.out) + (first + (int64_t)it * 256) * NP);
 #pragma unroll
     for (int q = 0; q < NP / 4; ++q) o[q] = make_int4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
