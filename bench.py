@@ -483,6 +483,33 @@ def batched_specs(count=256, seed=256):
     return out
 
 
+def batched_alg_bytes(ns, jmax):
+    """Algorithmic DRAM bytes of one batched launch over instances of these n
+    (int32 counts, theta and rho requested): every pass reads its whole input
+    and writes its whole output once -- the fold passes of up to jmax qubits
+    (the final pass at most two), theta and the exact integers T, then the
+    assembly (16-byte intermediates, complex64 rho)."""
+    total = 0
+    for n in ns:
+        r, C, in_sz = n, 1, 4
+        while r > 0:
+            J = min(r, jmax)
+            if r == 3 and J == 3:
+                J = 2
+            total += 6 ** r * C * in_sz
+            total += 4 ** n * 16 if J == r else 6 ** (r - J) * 4 ** J * C * 4
+            r, C, in_sz = r - J, C * 4 ** J, 4
+        t = 0
+        if n >= 6:
+            total += 4 ** n * 8 + 4 ** n * (16 if n > 6 else 8)
+            t = 6
+        while t < n:
+            J = 2 if n - t >= 2 else 1
+            total += 4 ** n * (8 if t == 0 else 16) + 4 ** n * (8 if t + J == n else 16)
+            t += J
+    return total
+
+
 def run_batched(args):
     """256 instances (n ~ U{3..9}, random-rank Ginibre mixtures, shots
     log-uniform in 500..10000, int32 counts) in one persistent launch, against
@@ -541,6 +568,9 @@ def run_batched(args):
     same = all(torch.equal(a, it[3]) for a, it in zip(theta_b, items))
     lre.lre_sync(ctx, stream)
     peak, peak_kind = load_peaks()
+    sched = lre.lre_batch_schedule(ctx)
+    alg = batched_alg_bytes([n for n, _, _, _ in specs], sched["jmax"])
+    achieved = alg / (ms_batch / 1e3) / 1e9
     out = {
         "metric": "Pauli bases/sec (batched instances)", "value": round(bases / (ms_batch / 1e3), 1),
         "unit": "Pauli bases/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -549,7 +579,12 @@ def run_batched(args):
         "config": {"workload": "256 instances, n ~ U{3..9}, random-rank (1..4) Ginibre mixtures, "
                                "shots/basis log-uniform 500..10000, int32 counts",
                    "bases": bases, "count_bytes": count_bytes,
-                   "schedule": dict(lre.lre_batch_schedule(ctx), tuned_ms=round(tuned_ms, 4))},
+                   "schedule": dict(sched, tuned_ms=round(tuned_ms, 4))},
+        "roofline": {"bound": "hbm", "kernel": "batch_kernel", "achieved": round(achieved, 1), "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "alg_bytes_per_launch": alg,
+                     "alg_bytes": "every pass reads its input and writes its output once: counts, fold "
+                                  "partials, theta and T, assembly intermediates, rho"},
         "batched": {"ms": round(ms_batch, 4), "launches_per_step": batch_launches,
                     "count_gbs": round(count_bytes / (ms_batch / 1e3) / 1e9, 1),
                     "frac_hbm_counts": round(count_bytes / (ms_batch / 1e3) / 1e9 / peak, 4)},

@@ -139,3 +139,16 @@ def test_rejected_descriptors(lib):
     assert f(ctypes.cast(arr, ctypes.c_void_p), 1, 3, 1024, 1024, None, 0) == -1
     arr = _descs(lre, [(4, I32, 0, True)])  # no shots
     assert f(ctypes.cast(arr, ctypes.c_void_p), 1, 3, 1024, 1024, None, 0) == -1
+
+
+def test_batched_byte_model_by_hand():
+    """bench.py's algorithmic bytes of a batched launch, for shapes worked by
+    hand: n = 1 (one final fold pass 6 x 4 B in, theta + T 4 x 16 B out; one
+    assembly pass 4 x 8 B in, 4 x 8 B out) and n = 4 at jmax 3 (fold 3 + 1
+    qubits; assembly 2 + 2 qubits)."""
+    import bench
+    assert bench.batched_alg_bytes([1], 3) == 24 + 64 + 32 + 32
+    fold4 = (6 ** 4 * 4 + 6 * 64 * 4) + (6 * 64 * 4 + 256 * 16)
+    asm4 = (256 * 8 + 256 * 16) + (256 * 16 + 256 * 8)
+    assert bench.batched_alg_bytes([4], 3) == fold4 + asm4
+    assert bench.batched_alg_bytes([1, 4], 3) == 152 + fold4 + asm4
