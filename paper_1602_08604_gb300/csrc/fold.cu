@@ -886,6 +886,24 @@ __global__ void debug_div_kernel(const int64_t *S, int64_t count, int64_t D, dou
 }  // namespace
 }  // namespace lre
 
+// Test hook (not part of include/lre.h; host only, no device work): the
+// fold pass schedule for these arguments.  Per pass, 9 int64 at out + 9 k:
+// first6, fused9, J, r, in_t, acc_t, mode, C, out_bytes (at most max_passes
+// written).  Returns the number of passes, or -1 for n outside 1..14.
+extern "C" int lre_debug_fold_plan(int n, int kind, int weighted, int parity, int64_t shots_bound, int aligned16,
+                                   int variant, int64_t *out, int max_passes) {
+  using namespace lre;
+  if (n < 1 || n > 14) return -1;
+  const auto plan = make_plan(n, static_cast<lre_count_kind>(kind), weighted != 0, parity != 0, shots_bound,
+                              aligned16 != 0, variant);
+  for (int k = 0; out && k < (int)plan.size() && k < max_passes; ++k) {
+    const PassPlan &p = plan[k];
+    const int64_t v[9] = {p.first6, p.fused9, p.J, p.r, p.in_t, p.acc_t, p.mode, p.C, (int64_t)p.out_bytes};
+    for (int f = 0; f < 9; ++f) out[9 * k + f] = v[f];
+  }
+  return (int)plan.size();
+}
+
 // Test hook (not part of include/lre.h): out[i] = the final pass's correctly
 // rounded S[i] / D (device arrays of `count`), for 0 < D < 2^53.
 extern "C" lre_status lre_debug_div(lre_ctx *ctx, const int64_t *S, int64_t count, int64_t D, double *out,
