@@ -291,3 +291,28 @@ def test_entry_spot_values_match_full_direct_sum():
     np.testing.assert_array_equal(direct.parity_sum_entries(n, idx, lambda b: c[b]), S[idx])
     assert direct.compatible_bases(0, 1) == [0, 1, 2]
     assert direct.compatible_bases(4 * 3 + 0, 2) == [6, 7, 8]   # Z(x)I: a_1 = Z
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_estimate_entries_match_full_estimate_every_k(n):
+    # the per-entry checker used at full size (S_i / (N 3^k) over the 3^k
+    # compatible groups) against the full direct sum, bit for bit, on every
+    # index (so every identity count k = 0..n), and against the explicit
+    # least-squares solve of Eq. (3) at n = 4 (independent of both)
+    N = 997
+    rng = np.random.default_rng(40 + n)
+    p = rng.dirichlet(np.ones(2 ** n), size=3 ** n)
+    c = np.stack([rng.multinomial(N, row) for row in p]).astype(np.int32)
+    idx = np.arange(4 ** n)
+    t_entries = direct.estimate_entries(n, idx, lambda b: c[b], N)
+    t_full = direct.estimate(c, N, n)
+    np.testing.assert_array_equal(t_entries, t_full)
+    ks = np.array([direct.identity_letters(i, n) for i in idx])
+    assert set(ks.tolist()) == set(range(n + 1))
+    if n == 4:
+        t_ls = explicit.expectations_from_theta(explicit.ls_theta(c, N, n), n)
+        assert np.max(np.abs(t_entries - t_ls)) < 1e-12
+    # identity letters are counted per base-4 digit, whatever its position
+    assert direct.identity_letters(0, n) == n
+    assert direct.identity_letters(3 * 4 ** (n - 1), n) == n - 1     # Z on qubit 1
+    assert direct.identity_letters(1, n) == n - 1                    # X on qubit n
