@@ -58,9 +58,13 @@ typedef enum {
   LRE_ERR_EIG_FAILED = 7      /* the Hermitian eigensolver reported failure   */
 } lre_status;
 
+/* Layout of the per-basis measurement results (Sec. III: the results of the
+ * 6^n operators are stored per basis group, 3^n groups of 2^n outcomes). */
 typedef enum {
-  LRE_COUNTS_I32 = 0, /* int32 counts */
-  LRE_COUNTS_I16 = 1  /* int16 counts (each count <= 32767)                   */
+  LRE_COUNTS_I32 = 0, /* int32 counts [3^n][2^n]                                  */
+  LRE_COUNTS_I16 = 1, /* int16 counts [3^n][2^n] (each count <= 32767)            */
+  LRE_SHOTS_U16 = 2   /* uint16 shot records [3^n][N]: outcome index of each shot
+                         (lre_estimate with uniform shots N only)                 */
 } lre_count_kind;
 
 typedef enum {
@@ -97,8 +101,10 @@ void lre_destroy(lre_ctx *ctx);
  * plan needs more returns LRE_ERR_OOM without enqueuing anything. */
 lre_status lre_set_workspace_limit(lre_ctx *ctx, size_t bytes);
 
-/* Workspace bytes lre_estimate needs for this n and count kind
- * (per_basis_shots != 0 for the per-basis FP64 weighting). */
+/* Workspace bytes lre_estimate needs for this n and count kind, rho
+ * included (per_basis_shots != 0 for the per-basis FP64 weighting; for
+ * LRE_SHOTS_U16 the dense int16 counts the records are histogrammed into,
+ * i.e. at most 32767 shots per basis). */
 lre_status lre_workspace_size(lre_ctx *ctx, int n, lre_count_kind kind, int per_basis_shots,
                               size_t *bytes);
 
@@ -119,12 +125,20 @@ lre_status lre_parity_sums(lre_ctx *ctx, const void *counts, lre_count_kind kind
  *   theta[i] = (sum_b Shat_b[i] / N_b) / 3^k (per-basis shots N_b)
  * with k(i) the number of identity letters of i, then, when rho != NULL,
  * Eq. (4): rho = (1/2^n) sum_i theta[i] P_i.
- * counts: device [3^n][2^n]; shots: device int64 [3^n] per-basis totals, or
- * NULL to use shots_uniform (> 0) for every basis; theta: device FP64 [4^n];
- * rho: device complex64 [2^n][2^n] or NULL.  With uniform shots theta is the
- * correctly rounded quotient of two exact integers.  When the counts' grand
- * total differs from shots_uniform * 3^n, LRE_ERR_SHOTS_MISMATCH is latched
- * (returned by lre_sync). */
+ * counts: device [3^n][2^n] counts (LRE_COUNTS_*), or device uint16 shot
+ * records [3^n][shots_uniform] (LRE_SHOTS_U16, which the call histograms into
+ * dense counts in its workspace; a record >= 2^n latches
+ * LRE_ERR_INVALID_ARG); shots: device int64 [3^n] per-basis totals (counts
+ * only), or NULL to use shots_uniform (> 0) for every basis; theta: device
+ * FP64 [4^n]; rho: device complex64 [2^n][2^n] or NULL.  With uniform shots
+ * theta is the correctly rounded quotient of two exact integers.  When the
+ * counts' grand total differs from shots_uniform * 3^n,
+ * LRE_ERR_SHOTS_MISMATCH is latched (returned by lre_sync).  Every count must
+ * lie in [0, shots_uniform]: the tensor-core first pass (lre_set_fold_path)
+ * reads counts in a form where a larger value would change the result, so it
+ * checks every count it reads and latches LRE_ERR_SHOTS_MISMATCH for one
+ * outside that range (theta is then not defined); the FWHT path computes the
+ * exact sums of whatever counts it is given. */
 lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, const int64_t *shots,
                         int64_t shots_uniform, int n, double *theta, lre_c64 *rho,
                         lre_stream stream);
@@ -142,10 +156,14 @@ lre_status lre_assemble(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
  * library holds until the process exits.  Runs on the calling thread's
  * current device, on `stream`.  1 <= n <= 10; a larger n returns
  * LRE_ERR_UNSUPPORTED (the scratch would not fit) and enqueues nothing.
- * The first call on a device looks up the array's device address (make it
- * before any stream capture).  All calls share the array: calls that
- * overlap on the GPU race on it and must be serialised by the caller.  No
- * part of the array needs to start at zero. */
+ * CUDA loads device code and variables lazily, so the first call on a device
+ * sets it up: it loads the array and the assembly kernels (about 32 MiB of
+ * device memory must be free then) and looks up the array's device address.
+ * Make that first call at start-up, before your allocator reserves the
+ * device and before any stream capture; later calls allocate nothing.  All
+ * calls share the array: calls that overlap on the GPU race on it and must
+ * be serialised by the caller.  No part of the array needs to start at
+ * zero.  On failure, lre_last_error(NULL) gives the reason (per thread). */
 lre_status lre_assemble_noalloc(const double *theta, int n, lre_c64 *rho, lre_stream stream);
 
 /* Step (iii): rho_out = argmin over density matrices sigma of
@@ -159,7 +177,8 @@ lre_status lre_assemble_noalloc(const double *theta, int n, lre_c64 *rho, lre_st
 lre_status lre_project(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_out,
                        double *eig_mu, double *eig_rho, lre_stream stream);
 
-/* Count ingest from shot records: counts[b][o] = #{s : records[b][s] == o}.
+/* Count ingest from shot records (Sec. III: the measured results are stored
+ * per basis group): counts[b][o] = #{s : records[b][s] == o}.
  * records: device uint16 [num_bases][shots_per_basis]; counts: device
  * [num_bases][2^n] of `kind`, overwritten.  A record >= 2^n latches
  * LRE_ERR_INVALID_ARG. */
@@ -167,7 +186,8 @@ lre_status lre_histogram(lre_ctx *ctx, const uint16_t *records, int64_t num_base
                          int64_t shots_per_basis, int n, void *counts, lre_count_kind kind,
                          lre_stream stream);
 
-/* Steps (i)+(ii) end to end from HOST memory.  host_in: pinned host buffer
+/* Steps (i)+(ii) end to end from HOST memory (Sec. II steps (i) and (ii) on
+ * the per-basis results of Sec. III, as lre_estimate).  host_in: pinned host buffer
  * of `host_kind` (dense counts, or shot records that the ingest kernel
  * histograms on the device); shots_uniform: shots per basis (> 0);
  * theta_host: host FP64 [4^n]; rho_host: host complex64 [2^n][2^n] or NULL.
@@ -249,7 +269,9 @@ lre_status lre_sync(lre_ctx *ctx, lre_stream stream);
 /* Static text for a status code. */
 const char *lre_status_string(lre_status s);
 
-/* Text of the last CUDA / library error seen by this context ("" if none). */
+/* Text of the last CUDA / library error seen by this context ("" if none);
+ * with ctx NULL, the reason for the last failure of lre_assemble_noalloc on
+ * the calling thread. */
 const char *lre_last_error(lre_ctx *ctx);
 
 /* Tracing: when enabled, every kernel launch (and every cuSOLVER / cuBLAS

@@ -162,6 +162,8 @@ constexpr int kMaxN = 14;
 
 lre_status check_ctx(lre_ctx *ctx) { return ctx ? LRE_OK : LRE_ERR_INVALID_ARG; }
 
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 lre_status check_n(int n) {
   if (n < 1) return LRE_ERR_INVALID_ARG;
   if (n > kMaxN) return LRE_ERR_UNSUPPORTED;
@@ -240,10 +242,14 @@ lre_status lre_workspace_size(lre_ctx *ctx, int n, lre_count_kind kind, int per_
   if (check_ctx(ctx) != LRE_OK || !bytes) return LRE_ERR_INVALID_ARG;
   lre_status st = check_n(n);
   if (st != LRE_OK) return st;
-  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
-  const size_t f = fold_workspace_bytes(n, kind, per_basis_shots != 0, per_basis_shots ? 0 : 1, ctx->first_variant);
+  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16 && kind != LRE_SHOTS_U16) return LRE_ERR_INVALID_ARG;
+  if (kind == LRE_SHOTS_U16 && per_basis_shots) return LRE_ERR_INVALID_ARG;
+  const lre_count_kind ck = kind == LRE_SHOTS_U16 ? LRE_COUNTS_I16 : kind;
+  const size_t f = fold_workspace_bytes(n, ck, per_basis_shots != 0, per_basis_shots ? 0 : 1, ctx->first_variant);
   const size_t a = assemble_workspace_bytes(n);
-  *bytes = f > a ? f : a;
+  const size_t t = per_basis_shots ? 0 : up256((size_t)8 << (2 * n));  // exact-integer assembly
+  const size_t dense = kind == LRE_SHOTS_U16 ? up256((size_t)ipow(3, n) * ((size_t)1 << n) * 2) : 0;
+  *bytes = (f > a ? f : a) + t + dense;
   return LRE_OK;
 }
 
@@ -267,18 +273,31 @@ lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, c
   if (check_ctx(ctx) != LRE_OK || !counts || !theta) return LRE_ERR_INVALID_ARG;
   lre_status st = check_n(n);
   if (st != LRE_OK) return st;
-  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16) return LRE_ERR_INVALID_ARG;
+  if (kind != LRE_COUNTS_I32 && kind != LRE_COUNTS_I16 && kind != LRE_SHOTS_U16) return LRE_ERR_INVALID_ARG;
   if (!shots && shots_uniform <= 0) return LRE_ERR_INVALID_ARG;
+  // shot records: uniform shots only; histogrammed into dense counts in the
+  // workspace (int16 while a count cannot exceed 32767)
+  const bool records = kind == LRE_SHOTS_U16;
+  if (records && (shots || shots_uniform > INT32_MAX)) return LRE_ERR_INVALID_ARG;
+  const lre_count_kind ck = records ? (shots_uniform <= 32767 ? LRE_COUNTS_I16 : LRE_COUNTS_I32) : kind;
+  const size_t dense = records ? up256((size_t)ipow(3, n) * ((size_t)1 << n) * (ck == LRE_COUNTS_I16 ? 2 : 4)) : 0;
   if ((st = set_device(ctx)) != LRE_OK) return st;
-  const size_t f = fold_workspace_bytes(n, kind, shots != nullptr, shots ? 0 : shots_uniform, ctx->first_variant);
+  const size_t f = fold_workspace_bytes(n, ck, shots != nullptr, shots ? 0 : shots_uniform, ctx->first_variant);
   const size_t a = rho ? assemble_workspace_bytes(n) : 0;
   const size_t shared = f > a ? f : a;
   // uniform shots: rho is assembled from the exact integers T = S 3^(n-k)
   const bool int_asm = rho && !shots;
-  const size_t tbytes = int_asm ? (((size_t)8 << (2 * n)) + 255) & ~(size_t)255 : 0;
-  if ((st = ensure_workspace(ctx, shared + tbytes)) != LRE_OK) return st;
+  const size_t tbytes = int_asm ? up256((size_t)8 << (2 * n)) : 0;
+  if ((st = ensure_workspace(ctx, shared + tbytes + dense)) != LRE_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int64_t *T = int_asm ? reinterpret_cast<int64_t *>(static_cast<char *>(ctx->ws) + shared) : nullptr;
+  if (records) {
+    void *dc = static_cast<char *>(ctx->ws) + shared + tbytes;
+    st = histogram_run(ctx, static_cast<const uint16_t *>(counts), ipow(3, n), shots_uniform, n, dc, ck, s);
+    if (st != LRE_OK) return st;
+    counts = dc;
+    kind = ck;
+  }
   FoldArgs fa{counts, kind, n, shots, shots_uniform, theta, nullptr};
   fa.T = T;
   if ((st = fold_run(ctx, fa, ctx->ws, shared, s)) != LRE_OK) return st;
@@ -362,7 +381,7 @@ const char *lre_status_string(lre_status s) {
   return "unknown status";
 }
 
-const char *lre_last_error(lre_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+const char *lre_last_error(lre_ctx *ctx) { return ctx ? ctx->last_error.c_str() : lre::noalloc_last_error(); }
 
 lre_status lre_profile(lre_ctx *ctx, int enable) {
   if (check_ctx(ctx) != LRE_OK) return LRE_ERR_INVALID_ARG;

@@ -212,6 +212,29 @@ LastScaleArgs int_assembly_scale(int n, int64_t shots) {
   return ls;
 }
 
+// Load every kernel assemble_run may launch into the current device's
+// memory now (under lazy module loading a kernel's code is otherwise loaded,
+// and its device memory taken, at its first launch).
+lre_status assemble_preload() {
+  const void *kernels[] = {
+      reinterpret_cast<const void *>(assemble_low6<NumF64>),
+      reinterpret_cast<const void *>(assemble_high4<NumF64, true>),
+      reinterpret_cast<const void *>(assemble_high4<NumF64, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, true, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, true, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, true, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, true, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, false>)};
+  for (const void *k : kernels) {
+    cudaFuncAttributes attr;
+    if (cudaFuncGetAttributes(&attr, k) != cudaSuccess) return LRE_ERR_CUDA;
+  }
+  return LRE_OK;
+}
+
 lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
                         cudaStream_t s) {
   return run_passes<NumF64>(ctx, theta, n, rho, ws, LastScale{0.f, 0.f}, s);

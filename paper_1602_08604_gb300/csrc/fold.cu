@@ -687,9 +687,18 @@ __global__ void inv_shots_kernel(const int64_t *shots, double *w, int64_t B, int
 
 namespace {
 
+// Operand variant of the tensor-core first pass for this pass (0 raw int16,
+// 1 biased int16, 3 int32 in two planes), or -1 when the ALU pass runs.
+int tensor_variant(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
+  if (!pp.first6 || pp.fused9 || ctx->fold_path != 1 || !ctx->mma_operand || a.shots != nullptr ||
+      a.shots_uniform <= 0)
+    return -1;
+  const int v = pp.in_t == T_I16 ? ctx->mma_biased : (pp.in_t == T_I32 ? 3 : -1);
+  return v >= 0 && a.shots_uniform <= mma_max_count(v) ? v : -1;
+}
+
 bool tensor_first_pass(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
-  return pp.first6 && !pp.fused9 && ctx->fold_path == 1 && ctx->mma_operand && pp.in_t == T_I16 &&
-         a.shots == nullptr && a.shots_uniform > 0 && a.shots_uniform <= mma_max_count(ctx->mma_biased);
+  return tensor_variant(ctx, pp, a) >= 0;
 }
 
 }  // namespace
@@ -733,11 +742,12 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
     Launch L(ctx, "inv_shots", s);
     inv_shots_kernel<<<256, 256, 0, s>>>(a.shots, wgt, B, ctx->d_status);
   }
-  // The tensor-core first pass writes its partials (below 729 x 2047 < 2^21)
-  // as split planes (3 bytes instead of 4) when the next pass is a TMA-staged
-  // store pass that reads them back.
+  // The tensor-core first pass writes its partials (below 729 x shots, which
+  // must stay below 2^23) as split planes (3 bytes instead of 4) when the
+  // next pass is a TMA-staged store pass that reads them back.
   const bool planes = !plan.empty() && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
-                      plan[1].mode == M_STORE && plan[1].in_t == T_I32 && ctx->generic_tma && plan[1].C % 32 == 0;
+                      a.shots_uniform * 729 < (1ll << 23) && plan[1].mode == M_STORE && plan[1].in_t == T_I32 &&
+                      ctx->generic_tma && plan[1].C % 32 == 0;
   const void *in = a.counts;
   size_t k_begin = 0, k_end = plan.size();
   if (a.stage != 0) {
@@ -771,15 +781,16 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
                                              static_cast<int32_t *>(out), hi, pp.r, tile_begin, tile_end, s);
       if (st != LRE_OK) return st;
     } else if (tensor) {
-      if (!make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(0)) ||
-          !make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
+      const lre_count_kind mk = pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32;
+      if (!make_count_map(&tmap, in, mk, pp.r, ipow(3, pp.r), mma_box_rows(0)) ||
+          !make_count_map(&tmap_tail, in, mk, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
         ctx->last_error = "tensor map of the counts rejected";
         return LRE_ERR_CUDA;
       }
       const int64_t elems = ipow(6, pp.r - 6) * 4096;
       int8_t *hi = planes ? static_cast<int8_t *>(out) + elems * 2 : nullptr;
       lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), hi,
-                                     pp.r, ctx->mma_biased, tile_begin, tile_end, s);
+                                     pp.r, tensor_variant(ctx, pp, a), a.shots_uniform, tile_begin, tile_end, s);
       if (st != LRE_OK) return st;
     } else if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
         make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {

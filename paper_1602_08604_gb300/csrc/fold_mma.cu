@@ -1,4 +1,5 @@
-// Tensor-core form of the first fold pass (int16 counts below 2048).
+// Tensor-core form of the first fold pass (int16 counts below 2048, or int32
+// counts below 16384 as two planes).
 //
 // A tile is 729 basis rows x 64 outcomes: six qubits in the rows (alB: the
 // high three, alA: the low three) and six in the outcomes (olB, olA).  Its
@@ -18,24 +19,43 @@
 // an operand column block that is zero for alA = 25, so no row outside an alB
 // group enters a used column.
 //
-// Operand encoding, two variants:
+// Operand encodings (the variant V):
 //   RAW      the int16 count c < 2048 is used unchanged as fp16 bits, which
 //            encode exactly c * 2^-24 (subnormal below 1024, the first
 //            binade above); D = S * 2^-24.
 //   BIASED   a converter pass ORs 0x6400 into each count (c < 1024), giving
 //            fp16(1024 + c); D = S + 1024 * rowsum(Tt) = S + 1024 * 216 for
 //            plA = III and S otherwise.
-// Every partial sum is an integer multiple of the smallest unit below 2^24
-// units, so FP32 accumulation in TMEM is exact and the level-B warps recover
-// the same integer the ALU path computes.
+//   RECORDS  RAW, with the count tiles built in shared memory from shot
+//            records (below).
+//   SPLIT    int32 counts c < 16384 (the 256-byte rows land as TMA brings
+//            them, 216 rows per chunk, four chunks per tile): converter warps
+//            rewrite each row in place as two 128-byte planes, the low plane
+//            holding c mod 2048 as fp16 bits (c_lo * 2^-24, as RAW) and the
+//            high plane fp16(c_hi * 2^-13) with c_hi = c >> 11, so that
+//            c_lo * 2^-24 + c_hi * 2^-13 = c * 2^-24.  Each K-step issues one
+//            MMA per plane (same Tt operand, B stride 256 bytes per row) into
+//            the same accumulator: D = S * 2^-24 again.
+// Every partial sum is an integer multiple of 2^-24 below 2^22 units (216
+// counts of at most 16383), so FP32 accumulation in TMEM is exact and the
+// level-B warps recover the same integer the ALU path computes.
 //
-// Roles (256 threads, one CTA per SM):
-//   warp 0     TMA producer into a ring of 3 chunk slots (one chunk = 16 alB
-//              groups = 432 rows); a slot is released by tcgen05.commit once
-//              the MMAs reading it have completed
-//   warp 1     issues 14 MMAs (M = 128, K = 16) per chunk into the tile's
-//              accumulator (224 columns; two tile buffers in 512 columns)
-//   warps 2,3  BIASED only: convert each chunk in place (half the rows each)
+// Range check: the encodings are exact only for counts in range, so the
+// warps that do not build or convert (RAW: warps 2, 3) read every landed
+// count, and the converter warps check what they convert; a count above the
+// stated shots per basis (or negative) latches LRE_ERR_SHOTS_MISMATCH.  The
+// MMAs of a chunk wait for that pass over it.
+//
+// Roles (256 threads, 320 for SPLIT; one CTA per SM):
+//   warp 0     TMA producer into a ring of 3 chunk slots (RAW/BIASED: one
+//              chunk = 16 alB groups = 432 rows of 128 bytes; SPLIT: 8 alB
+//              groups = 216 rows of 256 bytes); a slot is released by
+//              tcgen05.commit once the MMAs reading it have completed
+//   warp 1     issues the MMAs (M = 128, K = 16) of each chunk into the
+//              tile's accumulator (224 columns; two tile buffers in 512)
+//   warps 2,3  RAW: range check; BIASED: range check and convert in place
+//              (half the rows each); SPLIT (with warps 8, 9): range check and
+//              plane conversion, two rows per warp at a time
 //   warps 4,5  level B of even tiles from TMEM lanes 0..63
 //   warps 6,7  level B of odd tiles from TMEM lanes 64..127 (rows 64..127 of
 //              the operand repeat Tt, so those lanes hold the same D)
@@ -58,10 +78,25 @@ namespace {
 
 using namespace passes;
 
+enum : int { V_RAW = 0, V_BIASED = 1, V_RECORDS = 2, V_SPLIT = 3 };
+
 constexpr int MMA_THREADS = 256;
 constexpr int MMA_R = 3;                       // ring slots of one chunk each
 constexpr int CHUNK_ROWS = 432;                // 16 alB groups x 27 rows
 constexpr int SLOT_BYTES = CHUNK_ROWS * 128;   // int16 rows of 64 outcomes
+constexpr int SPLIT_ROWS = 216;                // SPLIT: 8 alB groups x 27 int32 rows
+constexpr int SPLIT_TAIL = 81;                 // SPLIT: the last chunk, alB 24..26
+constexpr int64_t SPLIT_MAX = 16383;           // SPLIT: largest count (216 c < 2^22)
+static_assert(SPLIT_ROWS * 256 == SLOT_BYTES, "a SPLIT chunk fills one slot");
+// the last SPLIT chain (N = 32) reads alB = 27 (rows 81..107 of its chunk)
+static_assert(4 * 27 <= SPLIT_ROWS, "padded alB group stays in the slot");
+
+template <int V>
+struct MmaCfg {
+  static constexpr int CPT = V == V_SPLIT ? 4 : 2;           // chunks per tile
+  static constexpr int THREADS = V == V_SPLIT ? 320 : 256;   // + warps 8, 9 convert
+  static constexpr int CONV_WARPS = V == V_SPLIT ? 4 : 2;    // arrivals on conv: 32 each
+};
 constexpr int A_BYTES = 16 * 28 * 128;         // 128 x 224 fp16, core-matrix layout
 constexpr int OFF_RING = A_BYTES;
 constexpr int OFF_BAR = OFF_RING + MMA_R * SLOT_BYTES;
@@ -90,13 +125,15 @@ __device__ __forceinline__ int32_t d_to_int(uint32_t bits, float scale, int32_t 
 // shared-memory atomics (eight loads in flight per lane), make the
 // writes visible to the tensor cores (proxy fence) and arrive on the slot.
 // Tile rows are numbered from tile_begin / 2^(n-6) in entries and offs.
-template <bool BIASED, bool RECORDS>
-__global__ void __launch_bounds__(MMA_THREADS, 1)
+// shots: the shots per basis (the range of every count).
+template <int V>
+__global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
                     const uint4 *__restrict__ gA, int32_t *__restrict__ out, int8_t *__restrict__ out_hi, int n,
                     int64_t tile_begin, int64_t tile_end, const uint16_t *__restrict__ entries,
                     const int32_t *__restrict__ offs, int64_t shots, int *status) {
-  static_assert(!(BIASED && RECORDS), "records feed the raw-count operand");
+  constexpr bool BIASED = V == V_BIASED, RECORDS = V == V_RECORDS, SPLIT = V == V_SPLIT;
+  constexpr int CPT = MmaCfg<V>::CPT;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *Am = smem;
@@ -111,11 +148,11 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_oh = (1ll << n) >> 6;
 
-  for (int i = threadIdx.x; i < A_BYTES / 16; i += MMA_THREADS) reinterpret_cast<uint4 *>(Am)[i] = gA[i];
+  for (int i = threadIdx.x; i < A_BYTES / 16; i += MmaCfg<V>::THREADS) reinterpret_cast<uint4 *>(Am)[i] = gA[i];
   if (threadIdx.x == 0) {
     for (int i = 0; i < MMA_R; ++i) {
       sm103::mbar_init(&full[i], 1);
-      sm103::mbar_init(&conv[i], 64);
+      sm103::mbar_init(&conv[i], 32 * MmaCfg<V>::CONV_WARPS);
       sm103::mbar_init(&empty[i], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -137,7 +174,8 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
   };
   const int64_t tiles = tile_end - tile_begin;
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const int64_t total = my_tiles * 2;  // chunks of this CTA
+  const int64_t total = my_tiles * CPT;  // chunks of this CTA
+  const bool conv_warp = SPLIT ? (warp == 2 || warp == 3 || warp == 8 || warp == 9) : (warp == 2 || warp == 3);
 
   if (RECORDS && (warp == 0 || warp == 2 || warp == 3)) {
     const int bw = warp == 0 ? 0 : warp - 1;  // builder of chunks g = bw (mod 3): always slot bw
@@ -199,8 +237,8 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     if (lane == 0) {
       int64_t g = 0;
       for (; g < total && !*abort_flag; ++g) {
-        const int64_t tile = tile_begin + blockIdx.x + (g >> 1) * gridDim.x;
-        const int c = (int)(g & 1);
+        const int64_t tile = tile_begin + blockIdx.x + (g / CPT) * gridDim.x;
+        const int c = (int)(g % CPT);
         const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
         const int slot = (int)(g % MMA_R);
         if (g >= MMA_R && !sm103::mbar_wait(&empty[slot], (uint32_t)((g / MMA_R - 1) & 1), abort_flag)) {
@@ -208,13 +246,20 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
           break;
         }
         uint8_t *dst = ring + slot * SLOT_BYTES;
-        const int x = (int)(oh * 64), y = (int)(ah * 729 + c * 432);
-        sm103::mbar_arrive_expect_tx(&full[slot], (BOX_BIG + (c ? BOX_TAIL : BOX_BIG)) * 128);
-        sm103::tma_load_2d(dst, &map_big, x, y, &full[slot]);
-        if (c == 0)
-          sm103::tma_load_2d(dst + BOX_BIG * 128, &map_big, x, y + (int)BOX_BIG, &full[slot]);
-        else
-          sm103::tma_load_2d(dst + BOX_BIG * 128, &map_tail, x, y + (int)BOX_BIG, &full[slot]);
+        const int x = (int)(oh * 64);
+        if constexpr (SPLIT) {  // one box of int32 rows: 216, or 81 for alB 24..26
+          const int y = (int)(ah * 729 + c * SPLIT_ROWS);
+          sm103::mbar_arrive_expect_tx(&full[slot], (c < 3 ? SPLIT_ROWS : SPLIT_TAIL) * 256);
+          sm103::tma_load_2d(dst, c < 3 ? &map_big : &map_tail, x, y, &full[slot]);
+        } else {
+          const int y = (int)(ah * 729 + c * 432);
+          sm103::mbar_arrive_expect_tx(&full[slot], (BOX_BIG + (c ? BOX_TAIL : BOX_BIG)) * 128);
+          sm103::tma_load_2d(dst, &map_big, x, y, &full[slot]);
+          if (c == 0)
+            sm103::tma_load_2d(dst + BOX_BIG * 128, &map_big, x, y + (int)BOX_BIG, &full[slot]);
+          else
+            sm103::tma_load_2d(dst + BOX_BIG * 128, &map_tail, x, y + (int)BOX_BIG, &full[slot]);
+        }
       }
       for (int64_t q = g > MMA_R ? g - MMA_R : 0; q < g; ++q)  // drain in-flight loads
         for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
@@ -225,32 +270,47 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     int64_t g = 0;
     for (; g < total; ++g) {
       const int slot = (int)(g % MMA_R);
-      const int64_t lt = g >> 1;
-      const int c = (int)(g & 1);
+      const int64_t lt = g / CPT;
+      const int c = (int)(g % CPT);
       const int tb = (int)(lt & 1);
       if (c == 0 && lt >= 2 &&
           !sm103::mbar_wait(&tile_free[tb], (uint32_t)(((lt >> 1) - 1) & 1), abort_flag)) {
         give_up();
         break;
       }
-      if (!sm103::mbar_wait(BIASED ? &conv[slot] : &full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+      if (!sm103::mbar_wait(RECORDS ? &full[slot] : &conv[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
       if (lane == 0) {
         const uint32_t b_base = sm103::smem_addr(ring + slot * SLOT_BYTES);
-        const uint32_t d = tmem + tb * TILE_COLS + c * 128;
-        const uint32_t idesc = sm103::umma_idesc_f16(128, c ? 96 : 128);
+        if constexpr (SPLIT) {
+          const uint32_t d = tmem + tb * TILE_COLS + c * 64;
+          const uint32_t idesc = sm103::umma_idesc_f16(128, c < 3 ? 64 : 32);
 #pragma unroll 1
-        for (int kk = 0; kk < 14; ++kk) {
-          const int brow = kk < 13 ? 2 * kk : 25;
-          const uint64_t ad = sm103::umma_desc(a_base + kk * 256, 128, 28 * 128);
-          const uint64_t bd = sm103::umma_desc(b_base + brow * 128, 128, 27 * 128);
-          sm103::umma_f16(d, ad, bd, idesc, kk > 0);
+          for (int kk = 0; kk < 14; ++kk) {
+            const int brow = kk < 13 ? 2 * kk : 25;
+            const uint64_t ad = sm103::umma_desc(a_base + kk * 256, 128, 28 * 128);
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {  // low plane, then high plane of the same rows
+              const uint64_t bd = sm103::umma_desc(b_base + brow * 256 + pl * 128, 256, 27 * 256);
+              sm103::umma_f16(d, ad, bd, idesc, kk > 0 || pl > 0);
+            }
+          }
+        } else {
+          const uint32_t d = tmem + tb * TILE_COLS + c * 128;
+          const uint32_t idesc = sm103::umma_idesc_f16(128, c ? 96 : 128);
+#pragma unroll 1
+          for (int kk = 0; kk < 14; ++kk) {
+            const int brow = kk < 13 ? 2 * kk : 25;
+            const uint64_t ad = sm103::umma_desc(a_base + kk * 256, 128, 28 * 128);
+            const uint64_t bd = sm103::umma_desc(b_base + brow * 128, 128, 27 * 128);
+            sm103::umma_f16(d, ad, bd, idesc, kk > 0);
+          }
         }
-        sm103::umma_commit(&empty[slot]);                 // slot reusable when these finish
-        if (c == 1) sm103::umma_commit(&tile_done[tb]);   // whole tile accumulated
+        sm103::umma_commit(&empty[slot]);                       // slot reusable when these finish
+        if (c == CPT - 1) sm103::umma_commit(&tile_done[tb]);   // whole tile accumulated
       }
       __syncwarp();
     }
@@ -260,27 +320,67 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
       for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
         if (sm103::mbar_try_wait(&empty[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
     }
-  } else if (warp == 2 || warp == 3) {
-    if constexpr (BIASED && !RECORDS) {
-      for (int64_t g = 0; g < total; ++g) {
-        const int slot = (int)(g % MMA_R);
-        if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
-          give_up();
-          break;
-        }
-        const int rows = (g & 1) ? (int)(BOX_BIG + BOX_TAIL) : (int)(2 * BOX_BIG);
-        uint4 *v4 = reinterpret_cast<uint4 *>(ring + slot * SLOT_BYTES);
-#pragma unroll 4
-        for (int k = (warp - 2) * 32 + lane; k < rows * 8; k += 64) {  // counts -> fp16(1024 + c)
-          uint4 v = v4[k];
-          v.x |= 0x64006400u; v.y |= 0x64006400u; v.z |= 0x64006400u; v.w |= 0x64006400u;
-          v4[k] = v;
-        }
-        sm103::fence_proxy_async_smem();
-        sm103::mbar_arrive(&conv[slot]);
+  } else if (conv_warp) {
+    // range check of every landed count (and the BIASED / SPLIT conversion)
+    uint32_t mx = 0;  // SPLIT: largest count as unsigned; else the two 16-bit halves' maxima
+    for (int64_t g = 0; g < total; ++g) {
+      const int slot = (int)(g % MMA_R);
+      const int c = (int)(g % CPT);
+      if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+        give_up();
+        break;
       }
+      uint8_t *base = ring + slot * SLOT_BYTES;
+      if constexpr (SPLIT) {
+        const int rows = c < 3 ? SPLIT_ROWS : SPLIT_TAIL;
+        const int cw = warp < 4 ? warp - 2 : warp - 6;  // 0..3
+        const int q = lane & 15;                        // 16 bytes (4 counts) of a 256-byte row
+        for (int r0 = 2 * cw; r0 < rows; r0 += 8) {    // two rows per warp at a time
+          const int row = r0 + (lane >> 4);
+          const bool act = row < rows;
+          uint4 v = make_uint4(0, 0, 0, 0);
+          if (act) v = *reinterpret_cast<const uint4 *>(base + row * 256 + q * 16);
+          __syncwarp();  // the whole row is read before any lane rewrites it
+          if (act) {
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            uint32_t lo[4], hi[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              mx = max(mx, w[k]);
+              lo[k] = w[k] & 0x7FFu;                 // fp16 bits of c_lo * 2^-24
+              const uint32_t h = w[k] >> 11;
+              // fp16 bits of h * 2^-13: the float exponent of h lowered by 13,
+              // rebiased from 127 to 15, mantissa cut to 10 bits (exact, h < 2048)
+              hi[k] = h ? (__float_as_uint((float)h) >> 13) - (125u << 10) : 0u;
+            }
+            *reinterpret_cast<uint2 *>(base + row * 256 + q * 8) =
+                make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
+            *reinterpret_cast<uint2 *>(base + row * 256 + 128 + q * 8) =
+                make_uint2(hi[0] | (hi[1] << 16), hi[2] | (hi[3] << 16));
+          }
+        }
+      } else {
+        const int rows = c ? (int)(BOX_BIG + BOX_TAIL) : (int)(2 * BOX_BIG);
+        uint4 *v4 = reinterpret_cast<uint4 *>(base);
+#pragma unroll 4
+        for (int k = (warp - 2) * 32 + lane; k < rows * 8; k += 64) {
+          uint4 v = v4[k];
+          mx = __vmaxu2(__vmaxu2(mx, v.x), __vmaxu2(v.y, __vmaxu2(v.z, v.w)));
+          if constexpr (BIASED) {  // counts -> fp16(1024 + c)
+            v.x |= 0x64006400u; v.y |= 0x64006400u; v.z |= 0x64006400u; v.w |= 0x64006400u;
+            v4[k] = v;
+          }
+        }
+      }
+      if (BIASED || SPLIT) sm103::fence_proxy_async_smem();
+      sm103::mbar_arrive(&conv[slot]);
     }
-  } else {
+    // a count above the shots per basis (a negative one reads as a large
+    // unsigned value) is outside the encoding's exact range
+    const uint32_t top = SPLIT ? mx : max(mx & 0xFFFFu, mx >> 16);
+    const int64_t lim = BIASED ? (shots < 1023 ? shots : 1023) : shots;
+    if ((int64_t)top > lim) latch(status, LRE_ERR_SHOTS_MISMATCH);
+  } else if (warp >= 4 && warp < 8) {
     // warps 4,5: even tiles, TMEM lanes 0..63; warps 6,7: odd tiles, lanes 64..127
     const int pair = (warp - 4) >> 1;
     const int quarter = warp & 3;
@@ -373,27 +473,33 @@ std::vector<uint16_t> make_a_operand() {
 
 size_t mma_operand_bytes() { return A_BYTES; }
 uint32_t mma_box_rows(int which) { return which ? BOX_TAIL : BOX_BIG; }
-int64_t mma_max_count(int biased) { return biased ? 1023 : 2047; }
+int64_t mma_max_count(int variant) { return variant == 1 ? 1023 : (variant == 3 ? SPLIT_MAX : 2047); }
 
 // Launch the tensor-core first pass over tiles [tile_begin, tile_end) of an
-// n-qubit int16 count matrix (tile = ah * 2^(n-6) + oh).  out_hi == nullptr:
+// n-qubit count matrix (tile = ah * 2^(n-6) + oh): variant 0 (RAW) or 1
+// (BIASED) for int16 counts, 3 (SPLIT) for int32 counts.  out_hi == nullptr:
 // int32 partials at out; otherwise split planes, the low 16 bits at out (as
 // uint16) and the bits above at out_hi (int8), exact while every partial is
-// below 2^23 in magnitude (729 x 2047 < 2^21 here).  map_big / map_tail
-// are tensor maps of the counts with boxes of 216 / 81 rows x 64 outcomes;
-// a_dev holds the operand written by mma_operand_upload; every count must be
-// at most mma_max_count(biased).
+// below 2^23 in magnitude (729 x shots).  map_big / map_tail are tensor maps
+// of the counts (int16, or int32 for SPLIT) with boxes of 216 / 81 rows x 64
+// outcomes; a_dev holds the operand written by mma_operand_upload; shots is
+// the shots per basis, at most mma_max_count(variant): a count above it
+// latches LRE_ERR_SHOTS_MISMATCH.
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
-                          int32_t *out, int8_t *out_hi, int n, int biased, int64_t tile_begin, int64_t tile_end,
-                          cudaStream_t s) {
+                          int32_t *out, int8_t *out_hi, int n, int variant, int64_t shots, int64_t tile_begin,
+                          int64_t tile_end, cudaStream_t s) {
   const int64_t tiles = tile_end - tile_begin;
   if (tiles <= 0) return LRE_OK;
+  if (shots <= 0 || shots > mma_max_count(variant) || (variant != 0 && variant != 1 && variant != 3))
+    return LRE_ERR_UNSUPPORTED;
   const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
-  Launch L(ctx, "fold_first6_mma", s);
-  auto kern = biased ? fold_first6_mma<true, false> : fold_first6_mma<false, false>;
+  Launch L(ctx, variant == 3 ? "fold_first6_mma_split" : "fold_first6_mma", s);
+  auto kern = variant == 3 ? fold_first6_mma<V_SPLIT>
+                           : (variant == 1 ? fold_first6_mma<V_BIASED> : fold_first6_mma<V_RAW>);
+  const int threads = variant == 3 ? MmaCfg<V_SPLIT>::THREADS : MMA_THREADS;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
-  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, out_hi, n,
-                                           tile_begin, tile_end, nullptr, nullptr, 0, ctx->d_status);
+  kern<<<grid, threads, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, out_hi, n,
+                                       tile_begin, tile_end, nullptr, nullptr, shots, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }
@@ -410,7 +516,7 @@ lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_
   const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
   CUtensorMap unused{};
   Launch L(ctx, "fold_first6_mma_records", s);
-  auto kern = fold_first6_mma<false, true>;
+  auto kern = fold_first6_mma<V_RECORDS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
   kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(unused, unused, static_cast<const uint4 *>(a_dev), out, out_hi, n,
                                            tile_begin, tile_end, entries, offs, shots, ctx->d_status);

@@ -60,6 +60,8 @@ struct lre_ctx {
   int batch_unit = 256;         // batched schedule: items per unit of the other fold and assembly passes
   int batch_occupancy[2] = {0, 0};  // most resident CTAs per SM of batch_kernel<2>, <3>
   std::vector<lre_batch_entry> batch_cache;  // device pass tables of earlier batched calls
+  uint64_t batch_wait_ns = 0;   // batched kernel: bound of a dependency wait (0 = the default 2 s)
+  int batch_stall_phase = -1;   // test hook: the first dependent phase at or after it never becomes ready
   size_t host_chunk_bytes = 256ull << 20; // host-input streaming: bytes of input per chunk
   int records_direct = 0;                 // host shot records: 1 = always the records-fed first pass
   cudaStream_t copy_stream = nullptr;     // host-input streaming (lre_estimate_host)
@@ -138,6 +140,10 @@ bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, const void *b
 size_t assemble_workspace_bytes(int n);
 lre_status assemble_run(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, void *ws,
                         cudaStream_t s);
+// Load the kernels of assemble_run into the current device (see assemble.cu).
+lre_status assemble_preload();
+// Text of the last failure of lre_assemble_noalloc on the calling thread.
+const char *noalloc_last_error();
 // Exact-integer variant for uniform shots: T_i = S_i 3^(n-k_i) (= t_i N 3^n).
 lre_status assemble_int_run(lre_ctx *ctx, const int64_t *T, int n, int64_t shots, lre_c64 *rho,
                             void *ws, cudaStream_t s);
@@ -168,7 +174,9 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
 // ---- tensor-core first pass (fold_mma.cu) ----------------------------------------
 size_t mma_operand_bytes();
 uint32_t mma_box_rows(int which);    // TMA box rows: 0 the 216-row box, 1 the 81-row tail
-int64_t mma_max_count(int biased);   // largest count the operand encoding keeps exact
+// largest count the operand encoding keeps exact: variant 0 raw int16 (2047),
+// 1 biased int16 (1023), 3 int32 in two planes (16383)
+int64_t mma_max_count(int variant);
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
 // records grouped by count tile (records.cu) and the first pass over them
 lre_status tile_bucket_run(lre_ctx *ctx, const uint16_t *records, int64_t tile_rows, int64_t shots, int n,
@@ -177,8 +185,8 @@ lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_
                                   int64_t shots, int32_t *out, int8_t *out_hi, int n, int64_t tile_begin,
                                   int64_t tile_end, cudaStream_t s);
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
-                          int32_t *out, int8_t *out_hi, int n, int biased, int64_t tile_begin, int64_t tile_end,
-                          cudaStream_t s);
+                          int32_t *out, int8_t *out_hi, int n, int variant, int64_t shots, int64_t tile_begin,
+                          int64_t tile_end, cudaStream_t s);
 
 // ---- batched instances (one persistent launch) ---------------------------------
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);

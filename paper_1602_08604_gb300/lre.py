@@ -22,6 +22,7 @@ LRE_ERR_EIG_FAILED = 7
 
 LRE_COUNTS_I32 = 0
 LRE_COUNTS_I16 = 1
+LRE_SHOTS_U16 = 2
 
 LRE_FOLD_FWHT = 0
 LRE_FOLD_TENSOR = 1
@@ -120,7 +121,9 @@ def _kind(t):
 
 def _check(st, ctx=None):
     if st != LRE_OK:
-        detail = load().lre_last_error(ctx).decode() if ctx else ""
+        # with no context, lre_last_error(NULL) holds the calling thread's
+        # lre_assemble_noalloc failure (empty for the other calls)
+        detail = load().lre_last_error(ctx).decode()
         raise LreError(st, detail)
 
 
@@ -150,13 +153,16 @@ def lre_parity_sums(ctx, counts, n, S, row_total_bound=0, stream=None):
                                   _ptr(S), _stream(stream)), ctx)
 
 
-def lre_estimate(ctx, counts, shots, n, theta, rho=None, stream=None):
-    """shots: int (uniform) or an int64 device tensor of per-basis totals."""
+def lre_estimate(ctx, counts, shots, n, theta, rho=None, stream=None, kind=None):
+    """shots: int (uniform) or an int64 device tensor of per-basis totals.
+    kind: LRE_COUNTS_* from the tensor's dtype by default; LRE_SHOTS_U16 for
+    a [3^n][shots] tensor of 16-bit shot records (any 16-bit dtype)."""
     if isinstance(shots, int):
         sp, su = None, shots
     else:
         sp, su = _ptr(shots), 0
-    _check(load().lre_estimate(ctx, _ptr(counts), _kind(counts), sp, int(su), int(n), _ptr(theta),
+    k = _kind(counts) if kind is None else int(kind)
+    _check(load().lre_estimate(ctx, _ptr(counts), k, sp, int(su), int(n), _ptr(theta),
                                _ptr(rho), _stream(stream)), ctx)
 
 

@@ -41,7 +41,7 @@ def _sums_by_path(torch, c, n, bound, biased=0):
             lre.lre_parity_sums(ctx, c, n, S, row_total_bound=bound)
             lre.lre_sync(ctx)
             names = [k for k, _ in lre.lre_profile_records(ctx)]
-            assert ("fold_first6_mma" in names) == tensor, names
+            assert any(k.startswith("fold_first6_mma") for k in names) == tensor, names
             res.append(S)
         finally:
             lre.lre_destroy(ctx)

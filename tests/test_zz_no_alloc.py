@@ -41,6 +41,25 @@ def test_noalloc_matches_lre_assemble_on_consecutive_calls():
         lre.lre_destroy(ctx)
 
 
+def test_noalloc_second_call_takes_no_device_memory():
+    """After the first call on the device has loaded the scratch array and the
+    kernels, a call leaves the device's free memory exactly as it was."""
+    torch = need_gpu()
+    from paper_1602_08604_gb300 import lre
+    n = 10
+    d = 2 ** n
+    theta = torch.from_numpy(_theta(n, 3)).cuda()
+    rho = torch.empty((d, d), dtype=torch.complex64, device="cuda")
+    lre.lre_assemble_noalloc(theta, n, rho)          # set-up call
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        lre.lre_assemble_noalloc(theta, n, rho)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     torch = need_gpu()
     from paper_1602_08604_gb300 import lre
@@ -49,3 +68,4 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(lre.LreError) as e:
         lre.lre_assemble_noalloc(theta, 11, rho)
     assert e.value.status == lre.LRE_ERR_UNSUPPORTED
+    assert "n <= 10" in str(e.value)                  # the reason is readable without a context
