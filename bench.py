@@ -36,6 +36,9 @@ WORKLOADS = {
     "n12s": dict(n=12, state="ghz", p=0.05, shots=1000, kind="i16", seed=12,
                  desc="n=12 GHZ+5% white noise, 531441 bases x 4096 outcomes, 1000 shots/basis, "
                       "int16 counts (profiling-size case of the n=14 kernels)"),
+    "n11p": dict(n=11, state="product", shrink=0.95, shots=4096, kind="i32", seed=11,
+                 desc="n=11 product of Haar single-qubit states, 5% depolarising, 177147 bases x 2048 "
+                      "outcomes, 4096 shots/basis, int32 counts (profiling-size case of the n=12 kernels)"),
     "n10": dict(n=10, state="ghz", p=0.10, shots=1000, kind="i32", seed=10,
                 desc="n=10 GHZ+10% white noise, 59049 bases x 1024 outcomes, 1000 shots/basis, int32"),
 }
@@ -311,6 +314,93 @@ def run_e2e(args, wl, lre, torch, device, theta_dev):
             "theta_equals_device_path": same}
 
 
+FIRST_PASS_KERNELS = ("fold_first6", "fold_first6_mma", "fold_first6_mma_split", "fold_first9_fused",
+                      "fold_first6_mma_records")
+
+
+def timed_steps(lre, ctx, torch, stream, step, steps, warmup):
+    """warmup untimed steps, then `steps` steps between CUDA events on the
+    launching stream, with the library's per-launch event records on.
+    Returns (ms per step, [(kernel, ms)], own kernel launches)."""
+    for _ in range(warmup):
+        step()
+    lre.lre_sync(ctx, stream)
+    torch.cuda.synchronize()
+    launches0 = lre.lre_launch_count(ctx)
+    lre.lre_profile(ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    lre.lre_sync(ctx, stream)
+    recs = lre.lre_profile_records(ctx)
+    lre.lre_profile(ctx, False)
+    return total_ms, recs, lre.lre_launch_count(ctx) - launches0
+
+
+def kernel_roofline(recs, steps, wl, workload):
+    """Per-kernel device time and the roofline of the step's dominant kernel
+    (algorithmic bytes per launch: the counts it reads once)."""
+    per = {}
+    for name, t in recs:
+        a = per.setdefault(name, [0.0, 0])
+        a[0] += t
+        a[1] += 1
+    top_name, (top_ms, top_n) = max(per.items(), key=lambda kv: kv[1][0])
+    avg_ms = top_ms / top_n
+    n = wl["n"]
+    count_bytes = 2 if wl["kind"] == "i16" else 4
+    alg_bytes = 3 ** n * (2 ** n) * count_bytes if top_name in FIRST_PASS_KERNELS else None
+    peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if alg_bytes else None
+    roofline = {"bound": "hbm", "kernel": top_name,
+                "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": recorded_traffic(top_name, workload),
+                "kernel_ms": round(avg_ms, 3),
+                "alg_bytes_per_launch": alg_bytes}
+    kernels = {k: {"ms_per_step": round(v[0] / steps, 3), "launches": v[1]} for k, v in per.items()}
+    return roofline, kernels
+
+
+def step_alg_bytes(wl):
+    """Counts read once, theta written (and read by the assembly), rho written."""
+    n = wl["n"]
+    return 3 ** n * (2 ** n) * (2 if wl["kind"] == "i16" else 4) + 8 * 4 ** n * 2 + 8 * 4 ** n
+
+
+def arm_record(lre, torch, device, stream, counts, wl, workload, path, steps, warmup, theta_ref=None):
+    """One timed arm of lre_estimate on resident counts with the first fold
+    pass on the tensor cores or on the ALUs (FWHT), in a context of its own."""
+    n = wl["n"]
+    ctx = lre.lre_create(device.index)
+    try:
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if path == "tensor" else lre.LRE_FOLD_FWHT)
+        theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
+        rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
+        total_ms, recs, launches = timed_steps(
+            lre, ctx, torch, stream, lambda: lre.lre_estimate(ctx, counts, wl["shots"], n, theta, rho, stream=stream),
+            steps, warmup)
+    finally:
+        lre.lre_destroy(ctx)
+    ms = total_ms / steps
+    roofline, kernels = kernel_roofline(recs, steps, wl, workload)
+    peak, _ = load_peaks()
+    sa = step_alg_bytes(wl)
+    out = {"fold_path": path, "ms_per_step": round(ms, 3), "value": round(3 ** n / (ms / 1e3), 1),
+           "unit": "Pauli bases/s", "steps": steps, "warmup": warmup, "gpu_launches": launches,
+           "roofline": roofline, "kernels": kernels, "step_alg_bytes": sa,
+           "step_frac": round(sa / (ms / 1e3) / 1e9 / peak, 4)}
+    if theta_ref is not None:
+        out["theta_equal_to_headline_arm"] = bool(torch.equal(theta, theta_ref))
+    return out, theta
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -339,20 +429,7 @@ def run_ours(args, wl):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = lre.lre_launch_count(ctx)
-    lre.lre_profile(ctx, True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    total_ms = ev0.elapsed_time(ev1)
-    lre.lre_sync(ctx, stream)
-    recs = lre.lre_profile_records(ctx)
-    lre.lre_profile(ctx, False)
-    launches = lre.lre_launch_count(ctx) - launches0
+    total_ms, recs, launches = timed_steps(lre, ctx, torch, stream, step, args.steps, 0)
     clk = clocks.stop()
     if world > 1:
         total_ms = max_over_ranks(total_ms, device)
@@ -360,40 +437,26 @@ def run_ours(args, wl):
     ms = total_ms / args.steps
     B = 3 ** n
     value = whole_job_rate(B, world, ms)
-
-    per = {}
-    for name, t in recs:
-        a = per.setdefault(name, [0.0, 0])
-        a[0] += t
-        a[1] += 1
-    top = max(per.items(), key=lambda kv: kv[1][0])
-    top_name, (top_ms, top_n) = top
-    avg_ms = top_ms / top_n
-    count_bytes = (2 if wl["kind"] == "i16" else 4)
-    alg_bytes = {  # algorithmic bytes per launch of each kernel
-        "fold_first6": B * (2 ** n) * count_bytes,
-        "fold_first6_mma": B * (2 ** n) * count_bytes,
-        "fold_first9_fused": B * (2 ** n) * count_bytes,
-    }.get(top_name)
-    peak, peak_kind = load_peaks()
-    achieved = alg_bytes / (avg_ms / 1e3) / 1e9 if alg_bytes else None
-    roofline = {"bound": "hbm", "kernel": top_name,
-                "achieved": round(achieved, 1) if achieved else None,
-                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / peak, 4) if achieved else None,
-                "traffic": recorded_traffic(top_name, args.workload),
-                "kernel_ms": round(avg_ms, 3),
-                "alg_bytes_per_launch": alg_bytes}
-    step_alg = B * (2 ** n) * count_bytes + 8 * 4 ** n * 2 + 8 * 4 ** n
-    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in per.items()}
+    roofline, kernels = kernel_roofline(recs, args.steps, wl, args.workload)
+    peak, _ = load_peaks()
+    step_alg = step_alg_bytes(wl)
     check = spot_check(torch, wl, theta, rho) if args.check and rank == 0 else None
+    compare = {}
+    if args.compare and rank == 0 and world == 1:
+        # the other first-pass arm on the same resident counts (spec:
+        # tensor-core form against the plain FWHT path, same accuracy)
+        other = "fwht" if args.fold_path == "tensor" else "tensor"
+        compare[f"{args.workload}_{other}"], _ = arm_record(
+            lre, torch, device, stream, counts, wl, args.workload, other, args.compare_steps, 2, theta_ref=theta)
+        torch.cuda.empty_cache()
     projection = None
     if args.project and rank == 0:
-        # step (iii), timed once on its own: FP64 tridiagonal reduction
-        # (cuSOLVER), bisection, Smolin correction, inverse iteration for the
-        # kept (or dropped) vectors, back-transformation and rank-k rebuild of
-        # the rho of the last step; achieved FP64 rate against a DGEMM measured
-        # in the same run
+        # step (iii), timed once on its own on the rho of the last step: the
+        # Lanczos path (FP64 products with mu, full reorthogonalisation, the
+        # threshold from the converged end of the spectrum, a certification
+        # run, the rank-k rebuild), or the tridiagonal reduction where it
+        # falls back; achieved FP64 rate against a DGEMM measured in the same
+        # run
         fp64_peak = fp64_gemm_tflops(torch, device)
         small = torch.eye(256, dtype=torch.complex64, device=device) / 256
         lre.lre_project(ctx, small, 8, torch.empty_like(small), stream=stream)  # handles and libraries warm
@@ -411,21 +474,35 @@ def run_ours(args, wl):
         kept = int((ev > 0).sum())
         d = 2 ** n
         m = min(kept, d - kept)
-        names = [k for k, _ in precs]
-        if "hetrd(cusolver)" in names:
-            # Hermitian tridiagonal reduction 16/3 d^3, back-transformation of m
-            # vectors 8 d^2 m, rank-m rebuild 4 d^2 m (real flops)
-            flops = 16.0 / 3.0 * d ** 3 + 8.0 * d * d * m + 4.0 * d * d * m
-            model = "16/3 d^3 (tridiagonal reduction) + 12 d^2 m (back-transformation, rank-m rebuild)"
+        ptab = {}
+        for k, v in precs:
+            a_ = ptab.setdefault(k, [0.0, 0])
+            a_[0] += v
+            a_[1] += 1
+        if "kry_matvec" in ptab:
+            # Lanczos path: the dominant kernel is the FP64 product with the
+            # promoted mu (4 complex FMAs = 8 d^2 flops per step)
+            mv_ms, steps = ptab["kry_matvec"]
+            achieved = 8.0 * d * d * steps / (mv_ms / 1e3) / 1e12
+            fp64 = {"bound": "fp64", "kernel": "kry_matvec", "achieved_tflops": round(achieved, 3),
+                    "peak_tflops": fp64_peak, "peak_source": "cuBLAS DGEMM 8192^3, same run",
+                    "frac": round(achieved / fp64_peak, 4), "lanczos_steps": steps,
+                    "flop_model": "8 d^2 per Lanczos step (complex FP64 matrix-vector product)"}
         else:
-            flops = 16.0 / 3.0 * d ** 3 + 8.0 * d ** 3 + 4.0 * d * d * m
-            model = "16/3 d^3 + 8 d^3 (full eigendecomposition) + 4 d^2 m (rank-m rebuild)"
-        achieved = flops / secs / 1e12
-        projection = {"seconds": round(secs, 4), "kernels_ms": {k: round(v, 3) for k, v in precs},
+            if "hetrd(cusolver)" in ptab:
+                flops = 16.0 / 3.0 * d ** 3 + 8.0 * d * d * m + 4.0 * d * d * m
+                model = "16/3 d^3 (tridiagonal reduction) + 12 d^2 m (back-transformation, rank-m rebuild)"
+            else:
+                flops = 16.0 / 3.0 * d ** 3 + 8.0 * d ** 3 + 4.0 * d * d * m
+                model = "16/3 d^3 + 8 d^3 (full eigendecomposition) + 4 d^2 m (rank-m rebuild)"
+            achieved = flops / secs / 1e12
+            fp64 = {"bound": "fp64", "achieved_tflops": round(achieved, 3), "peak_tflops": fp64_peak,
+                    "peak_source": "cuBLAS DGEMM 8192^3, same run", "frac": round(achieved / fp64_peak, 4),
+                    "flop_model": model}
+        projection = {"seconds": round(secs, 4),
+                      "kernels": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in ptab.items()},
                       "kept_eigenvalues": kept, "trace": float(ev.sum()), "min_eigenvalue": float(ev.min()),
-                      "fp64": {"bound": "fp64", "achieved_tflops": round(achieved, 3),
-                               "peak_tflops": fp64_peak, "peak_source": "cuBLAS DGEMM 8192^3, same run",
-                               "frac": round(achieved / fp64_peak, 4), "flop_model": model}}
+                      "fp64": fp64}
         del rho_p
     lre.lre_destroy(ctx)
     ctx = None
@@ -436,6 +513,24 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         e2e = run_e2e(args, wl, lre, torch, device, theta_keep)
+        del theta_keep
+    else:
+        del counts, rho
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if args.compare and rank == 0 and world == 1 and args.workload == "n14":
+        # the int32 precision workload (n = 12, 4096 shots per basis): the
+        # tensor-core form (two fp16 planes per count) against the FWHT path
+        wl12 = WORKLOADS["n12"]
+        c12 = make_counts(torch, wl12, device)
+        rec_t, th_t = arm_record(lre, torch, device, stream, c12, wl12, "n12", "tensor", args.compare_steps, 3)
+        rec_f, _ = arm_record(lre, torch, device, stream, c12, wl12, "n12", "fwht", args.compare_steps, 3,
+                              theta_ref=th_t)
+        compare["n12_tensor"], compare["n12_fwht"] = rec_t, rec_f
+        del c12, th_t
+        torch.cuda.empty_cache()
+        compare["batched"] = run_batched(args, summary=True)
+        torch.cuda.empty_cache()
 
     out = None
     if rank == 0:
@@ -461,6 +556,7 @@ def run_ours(args, wl):
             "kernels": kernels,
             "step_alg_bytes": step_alg,
             "step_alg_gbs": round(step_alg / (ms / 1e3) / 1e9, 1),
+            "step_frac": round(step_alg / (ms / 1e3) / 1e9 / peak, 4),
         }
         if check:
             out["parity"] = check
@@ -468,6 +564,8 @@ def run_ours(args, wl):
         if projection:
             out["projection"] = projection
             out["total_seconds_with_projection"] = round(ms / 1000 + projection["seconds"], 4)
+        if compare:
+            out["comparisons"] = compare
     return out
 
 
@@ -510,10 +608,11 @@ def batched_alg_bytes(ns, jmax):
     return total
 
 
-def run_batched(args):
+def run_batched(args, summary=False):
     """256 instances (n ~ U{3..9}, random-rank Ginibre mixtures, shots
     log-uniform in 500..10000, int32 counts) in one persistent launch, against
-    one lre_estimate call per instance."""
+    one lre_estimate call per instance.  summary: the record for the headline
+    line's comparisons (args.compare_steps timed steps)."""
     import numpy as np
     import torch
     from paper_1602_08604_gb300 import lre
@@ -538,22 +637,25 @@ def run_batched(args):
     bases = sum(3 ** n for n, _, _, _ in specs)
     count_bytes = sum(3 ** n * 2 ** n * 4 for n, _, _, _ in specs)
 
+    steps = args.compare_steps if summary else args.steps
+    warmup = args.warmup if not summary else 3
+
     def timed(fn):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps
+        return e0.elapsed_time(e1) / steps
 
     launches0 = lre.lre_launch_count(ctx)
     ms_batch = timed(lambda: lre.lre_batch_run(ctx, items, stream=stream))
-    batch_launches = (lre.lre_launch_count(ctx) - launches0) // (args.steps + args.warmup)
+    batch_launches = (lre.lre_launch_count(ctx) - launches0) // (steps + warmup)
     theta_b = [it[3].clone() for it in items]
     # the same launch captured once in a CUDA graph and replayed
     side = torch.cuda.Stream(device)
@@ -564,7 +666,7 @@ def run_batched(args):
     same_graph = all(torch.equal(a, it[3]) for a, it in zip(theta_b, items))
     launches0 = lre.lre_launch_count(ctx)
     ms_single = timed(lambda: [lre.lre_estimate(ctx, c, s, n, t, r, stream=stream) for c, s, n, t, r in items])
-    single_launches = (lre.lre_launch_count(ctx) - launches0) // (args.steps + args.warmup)
+    single_launches = (lre.lre_launch_count(ctx) - launches0) // (steps + warmup)
     same = all(torch.equal(a, it[3]) for a, it in zip(theta_b, items))
     lre.lre_sync(ctx, stream)
     peak, peak_kind = load_peaks()
@@ -573,8 +675,9 @@ def run_batched(args):
     achieved = alg / (ms_batch / 1e3) / 1e9
     out = {
         "metric": "Pauli bases/sec (batched instances)", "value": round(bases / (ms_batch / 1e3), 1),
-        "unit": "Pauli bases/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_batch, 4), "higher_is_better": True, "scaling": "weak",
+        "unit": "Pauli bases/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+        "ms_per_step": round(ms_batch, 4), "higher_is_better": True,
+        "scaling": "weak",
         "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
         "config": {"workload": "256 instances, n ~ U{3..9}, random-rank (1..4) Ginibre mixtures, "
                                "shots/basis log-uniform 500..10000, int32 counts",
@@ -591,25 +694,29 @@ def run_batched(args):
         "graph_replay": {"ms": round(ms_graph, 4), "theta_equal": same_graph},
         "one_launch_per_instance": {"ms": round(ms_single, 4), "launches_per_step": single_launches},
         "speedup_vs_per_instance": round(ms_single / ms_batch, 2),
-        "theta_equal_batched_vs_single": same, "gpu_launches": batch_launches * args.steps,
+        "theta_equal_batched_vs_single": same, "gpu_launches": batch_launches * steps,
     }
     lre.lre_destroy(ctx)
+    del items
+    if summary:
+        for k in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data"):
+            out.pop(k, None)
     return out
 
 
 def accuracy_point(lre, ctx, torch, n, shots, seed):
     """One point of the Sec. V / Fig. 3 study: the maximally mixed n-qubit
-    state measured with `shots` shots per basis (counts drawn on the device as
-    a product of unpolarised qubits; int32 above 32767 shots), through lre_estimate and
-    lre_project.  For the true state I/d every error needs only theta and
-    spectra: ||mu - I/d||_F^2 = sum_{P != I} t_P^2 / d, ||rho_hat - I/d||_F^2 =
-    sum (l_i - 1/d)^2 and the fidelity with I/d = (sum sqrt(l_i))^2 / d."""
-    import numpy as np
+    state measured with `shots` shots per basis (counts drawn on the device by
+    binary splitting of each basis' shots; int16 while the counts stay far
+    below 32767, int32 above), through lre_estimate and lre_project.  For the
+    true state I/d every error needs only theta and spectra: ||mu - I/d||_F^2 =
+    sum_{P != I} t_P^2 / d, ||rho_hat - I/d||_F^2 = sum (l_i - 1/d)^2 and the
+    fidelity with I/d = (sum sqrt(l_i))^2 / d."""
     from synth import gen
     d = 2 ** n
     dev = torch.device("cuda", 0)
-    counts = torch.empty((3 ** n, d), dtype=torch.int16 if shots <= 32767 else torch.int32, device=dev)
-    gen.gen_product(np.zeros((n, 3)), shots, seed, counts)
+    counts = torch.empty((3 ** n, d), dtype=torch.int16 if shots // d <= 16384 else torch.int32, device=dev)
+    gen.gen_mixed(n, shots, seed, counts)
     theta = torch.empty(4 ** n, dtype=torch.float64, device=dev)
     rho = torch.empty((d, d), dtype=torch.complex64, device=dev)
     lre.lre_estimate(ctx, counts, shots, n, theta, rho)
@@ -638,8 +745,8 @@ def run_accuracy(args):
     from paper_1602_08604_gb300 import lre
     ctx = lre.lre_create(0)
     try:
-        pts = [accuracy_point(lre, ctx, torch, args.study_n, s, 1000 + i)
-               for i, s in enumerate(args.study_shots)]
+        pts = [accuracy_point(lre, ctx, torch, args.study_n, int(round(n0 * 2 ** args.study_n)), 1000 + i)
+               for i, n0 in enumerate(args.study_n0)]
     finally:
         lre.lre_destroy(ctx)
     return {"study": "estimation error vs shots, maximally mixed state (Sec. V, Fig. 3)", "n": args.study_n,
@@ -676,9 +783,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="n14", choices=sorted(WORKLOADS) + ["batched", "accuracy"])
-    ap.add_argument("--study-n", type=int, default=12, help="qubits of the accuracy study")
-    ap.add_argument("--study-shots", type=int, nargs="+", default=[128, 256, 512, 1024, 2047],
-                    help="shots per basis of the accuracy study's points")
+    ap.add_argument("--study-n", type=int, default=14, help="qubits of the accuracy study")
+    ap.add_argument("--study-n0", type=float, nargs="+", default=[0.125, 1, 4, 16, 64],
+                    help="N_0 (shots per basis / 2^n) of the accuracy study's points")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--check", action="store_true", help="spot-check parity against the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -687,6 +794,10 @@ def main():
                     help="skip the one timed run of step (iii) (the projection)")
     ap.add_argument("--fold-path", default="tensor", choices=["fwht", "tensor"],
                     help="first fold pass on the tensor cores (the library default) or on the ALUs (FWHT)")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the comparison arms (the other first-pass path on the same counts; for the "
+                         "n=14 workload also the n=12 int32 workload on both paths and the batched launch)")
+    ap.add_argument("--compare-steps", type=int, default=5, help="timed steps of each comparison arm")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     args = ap.parse_args()

@@ -414,11 +414,13 @@ extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   return LRE_OK;
 }
 
-// Test hook (not part of include/lre.h): step (iii) through the
-// eigenvalue-first path (1, the default, for d >= 64) or always through the
-// full eigendecomposition (0).
+// Test hook (not part of include/lre.h): step (iii) through the default
+// choice (1: the Krylov path from d = 2048 on when eig_mu is not asked for,
+// else the eigenvalue-first path for d >= 64), always the eigenvalue-first
+// path with its tridiagonal reduction (2), or always the full
+// eigendecomposition (0).
 extern "C" lre_status lre_debug_set_project_mode(lre_ctx *ctx, int mode) {
-  if (!ctx || mode < 0 || mode > 1) return LRE_ERR_INVALID_ARG;
+  if (!ctx || mode < 0 || mode > 2) return LRE_ERR_INVALID_ARG;
   ctx->project_mode = mode;
   return LRE_OK;
 }

@@ -219,7 +219,8 @@ __device__ __forceinline__ int find_phase(const int64_t *begin, int nph, int64_t
 template <int JMAX>
 __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict__ ph, const int64_t *__restrict__ gbegin,
                                                    int nph, unsigned *__restrict__ done, BatchState *st,
-                                                   int64_t total_units, int tile_bytes, int *status) {
+                                                   int64_t total_units, int tile_bytes, uint64_t wait_ns,
+                                                   int *status) {
   // dynamic shared memory: [assembly tile (tile_bytes)][phase starts]
   extern __shared__ __align__(16) unsigned char bsmem[];
   int64_t *sbegin = reinterpret_cast<int64_t *>(bsmem + tile_bytes);
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BPhase *__restrict_
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(done + dep) : "memory");
             if (v >= need) break;
             if ((it & 63u) == 63u) {
-              if (*abort || sm103::globaltimer() - t0 > sm103::kWaitNs) {
+              if (*abort || sm103::globaltimer() - t0 > wait_ns) {
                 ok = 0;
                 break;
               }
@@ -500,10 +501,10 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   // A plan depends only on the descriptors and the schedule: an earlier call
   // with the same ones left its pass table in a device buffer (kept until
   // lre_destroy), so repeated and captured launches skip the host-side plan.
-  const int sched[3] = {jmax, ctx->batch_first_unit, ctx->batch_unit};
+  const int sched[4] = {jmax, ctx->batch_first_unit, ctx->batch_unit, ctx->batch_stall_phase};
   std::vector<char> key(sizeof(lre_instance) * (size_t)count + sizeof(sched));
   std::copy(reinterpret_cast<const char *>(inst), reinterpret_cast<const char *>(inst + count), key.begin());
-  std::copy(reinterpret_cast<const char *>(sched), reinterpret_cast<const char *>(sched + 3),
+  std::copy(reinterpret_cast<const char *>(sched), reinterpret_cast<const char *>(sched + 4),
             key.begin() + sizeof(lre_instance) * (size_t)count);
   const lre_batch_entry *hit = nullptr;
   for (const auto &en : ctx->batch_cache)
@@ -526,6 +527,12 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
     char *w = static_cast<char *>(ctx->ws);
     Plan plan = build_plan(inst, count, jmax, ctx->batch_first_unit, ctx->batch_unit, w + head);
     for (auto &b : plan.phases) b.g.status = ctx->d_status;
+    if (ctx->batch_stall_phase >= 0)  // test hook: one more unit than exists, so the wait runs out
+      for (size_t k = (size_t)ctx->batch_stall_phase; k < nph; ++k)
+        if (plan.phases[k].dep >= 0) {
+          plan.phases[k].dep_units += 1;
+          break;
+        }
     std::vector<char> tab(nph * (sizeof(BPhase) + sizeof(int64_t)));
     std::copy(reinterpret_cast<const char *>(plan.phases.data()),
               reinterpret_cast<const char *>(plan.phases.data()) + nph * sizeof(BPhase), tab.data());
@@ -586,14 +593,15 @@ lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStre
   const int tile_bytes = hit->tile_bytes;
   const int64_t total_units = hit->total_units;
   const size_t smem = tile_bytes + (nph <= (size_t)BATCH_SMEM_PHASES ? nph * sizeof(int64_t) : 0);
+  const uint64_t wait_ns = ctx->batch_wait_ns ? ctx->batch_wait_ns : sm103::kWaitNs;
   {
     Launch L(ctx, "batch_kernel", s);
     if (jmax >= 3)
       batch_kernel<3><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, total_units, tile_bytes,
-                                              ctx->d_status);
+                                              wait_ns, ctx->d_status);
     else
       batch_kernel<2><<<grid, 256, smem, s>>>(table, starts, (int)nph, done, bs, total_units, tile_bytes,
-                                              ctx->d_status);
+                                              wait_ns, ctx->d_status);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "batch kernel launch");
@@ -670,4 +678,19 @@ extern "C" int lre_debug_batch_plan(const lre_instance *descs, int count, int jm
     for (int f = 0; f < 8; ++f) out[8 * k + f] = v[f];
   }
   return nph;
+}
+
+// Test hook (not part of include/lre.h): failure injection for the batched
+// kernel's bounded waits.  wait_ms > 0 bounds every dependency wait of later
+// lre_batch_run calls by that many milliseconds (0 restores the default 2 s);
+// stall_phase >= 0 makes the first dependent phase of the pass table at or
+// after that index wait for one unit more than its dependency has, so its
+// units never become ready and their waits run out (LRE_ERR_TIMEOUT, every
+// CTA leaves); -1 turns that off.  Host-side table data only: no kernel is
+// changed.
+extern "C" lre_status lre_debug_batch_fault(lre_ctx *ctx, int wait_ms, int stall_phase) {
+  if (!ctx || wait_ms < 0 || stall_phase < -1) return LRE_ERR_INVALID_ARG;
+  ctx->batch_wait_ns = (uint64_t)wait_ms * 1000000ull;
+  ctx->batch_stall_phase = stall_phase;
+  return LRE_OK;
 }

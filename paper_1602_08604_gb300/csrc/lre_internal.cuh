@@ -159,7 +159,29 @@ lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
 // tridiagonal eigenproblem kernels (tridiag.cu)
 constexpr int TRI_THREADS = 256;
 __global__ void tri_bisect_kernel(const double *a, const double *b2, int64_t n, double lo0, double hi0, double tol,
-                                  double pivmin, double *W);
+                                  double pivmin, double *W, int64_t j0, int64_t cnt);
+// Gershgorin bounds of T (stats[0], stats[1]), the largest squared
+// off-diagonal (stats[2]) and the squares b2 (one CTA of 256 threads).
+__global__ void tri_prepare(const double *a, const double *b, int64_t n, double *b2, double *stats);
+
+// Smolin threshold: eigenvalues kept and the shift added to each.
+struct SmolinResult {
+  int64_t kept;
+  double shift;
+};
+// The projected matrix from m unit vectors Z (column-major d x m, the
+// eigenvectors of conj(mu)) and their eigenvalues w, in the kept form
+// sum (w + s) z z^dag or the dropped form mu + s I + sum -(w + s) z z^dag
+// (C holding conj(mu) column-major on entry), written to rho_out as
+// row-major complex64.  Z is scaled in place; C is the working matrix.
+lre_status rebuild_emit(lre_ctx *ctx, struct cublasContext *blas, double2 *C, double2 *Z, const double *w,
+                        int64_t d, int64_t m, bool kept_form, const SmolinResult *res, lre_c64 *rho_out,
+                        cudaStream_t s);
+// The Krylov projection (krylov.cu): *fallback = true, with nothing written to
+// the outputs, when it cannot decide or certify the threshold; eig_rho
+// (device, or NULL) is filled only in the kept form (*fallback otherwise).
+lre_status project_krylov(lre_ctx *ctx, struct cublasContext *blas, const lre_c64 *rho_in, int64_t d,
+                          lre_c64 *rho_out, double *eig_rho, cudaStream_t s, bool *fallback);
 constexpr int TRI_ROUNDS = 3;  // inverse-iteration rounds
 __global__ void tri_factor(const double *a, const double *b, int64_t n, const double *lam, int m, double tnorm,
                            double *lu);

@@ -37,11 +37,6 @@
 namespace lre {
 namespace {
 
-struct SmolinResult {
-  int64_t kept;
-  double shift;
-};
-
 __global__ void promote_kernel(const float2 *in, double2 *a, double2 *b, int64_t N) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -98,6 +93,8 @@ __global__ void to_complex(const double *X, double2 *Z, int64_t total) {
     Z[e] = make_double2(X[e], 0.0);
 }
 
+}  // namespace
+
 // Gershgorin bounds and norm of T, and the squared off-diagonal (one CTA).
 __global__ void tri_prepare(const double *a, const double *b, int64_t n, double *b2, double *stats) {
   __shared__ double lo_s[256], hi_s[256], bb_s[256];
@@ -127,6 +124,8 @@ __global__ void tri_prepare(const double *a, const double *b, int64_t n, double 
     stats[2] = bb_s[0];
   }
 }
+
+namespace {
 
 __global__ void add_diag(double2 *C, int64_t d, const SmolinResult *res) {
   const double s = res->shift;
@@ -204,12 +203,15 @@ lre_status get_handles(lre_ctx *ctx, cudaStream_t s, cusolverDnHandle_t &solver,
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
 // C <- the projected matrix from the m vectors Z (column-major d x m, unit
 // norm, eigenvalues w): kept form C = sum (w + s) z z^dag, or dropped form
 // C = mu + s I + sum -(w + s) z z^dag with C holding mu on entry; then the
 // complex64 row-major output.  Z is scaled in place.
-lre_status rebuild_emit(lre_ctx *ctx, cublasHandle_t blas, double2 *C, double2 *Z, const double *w, int64_t d,
+lre_status rebuild_emit(lre_ctx *ctx, cublasContext *blas_ctx, double2 *C, double2 *Z, const double *w, int64_t d,
                         int64_t m, bool kept_form, const SmolinResult *res, lre_c64 *rho_out, cudaStream_t s) {
+  cublasHandle_t blas = reinterpret_cast<cublasHandle_t>(blas_ctx);
   const int grid = ctx->num_sms * 8;
   if (kept_form) {
     {
@@ -253,6 +255,8 @@ lre_status rebuild_emit(lre_ctx *ctx, cublasHandle_t blas, double2 *C, double2 *
   return LRE_OK;
 }
 
+namespace {
+
 // Reads back the Smolin result and a cuSOLVER info word.
 lre_status read_back(lre_ctx *ctx, const SmolinResult *res, const int *info, const char *what, SmolinResult &hres,
                      cudaStream_t s) {
@@ -269,6 +273,7 @@ lre_status read_back(lre_ctx *ctx, const SmolinResult *res, const int *info, con
 }
 
 constexpr int64_t PARTIAL_MAX = 1024;  // most eigenvectors the eigenvalue-first path forms
+constexpr int64_t KRYLOV_MIN_D = 2048;  // smallest d the Krylov path takes
 
 // Eigenvalue-first projection; *fallback = true (nothing written to rho_out)
 // when the smaller of the kept and dropped sets exceeds PARTIAL_MAX.
@@ -341,7 +346,8 @@ lre_status project_partial(lre_ctx *ctx, cusolverDnHandle_t solver, cublasHandle
   {
     Launch L(ctx, "tri_bisect", s);
     tri_bisect_kernel<<<(int)((d + 127) / 128), 128, 0, s>>>(ta, tb2, d, hst[0] - pad, hst[1] + pad,
-                                                             4.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN), pivmin, W);
+                                                             4.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN), pivmin, W,
+                                                             0, d);
   }
   {
     Launch L(ctx, "smolin", s);
@@ -391,7 +397,7 @@ lre_status project_partial(lre_ctx *ctx, cusolverDnHandle_t solver, cublasHandle
       return LRE_ERR_EIG_FAILED;
     }
   }
-  if ((st = rebuild_emit(ctx, blas, C, Z, W + off, d, m, kept_form, res, rho_out, s)) != LRE_OK) return st;
+  if ((st = rebuild_emit(ctx, reinterpret_cast<cublasContext *>(blas), C, Z, W + off, d, m, kept_form, res, rho_out, s)) != LRE_OK) return st;
   int hinfo = 0;
   e = cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -413,7 +419,15 @@ lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
   cublasHandle_t blas;
   lre_status st0 = get_handles(ctx, s, solver, blas);
   if (st0 != LRE_OK) return st0;
-  if (ctx->project_mode == 1 && d >= 64) {
+  // Krylov path: without eig_mu (which asks for the whole spectrum), from
+  // d = 2048 on; it falls back to the tridiagonal reduction when it cannot
+  // decide or certify the threshold
+  if (ctx->project_mode == 1 && d >= KRYLOV_MIN_D && !eig_mu) {
+    bool fallback = false;
+    st0 = project_krylov(ctx, reinterpret_cast<cublasContext *>(blas), rho_in, d, rho_out, eig_rho, s, &fallback);
+    if (st0 != LRE_OK || !fallback) return st0;
+  }
+  if (ctx->project_mode >= 1 && d >= 64) {
     bool fallback = false;
     st0 = project_partial(ctx, solver, blas, rho_in, d, rho_out, eig_mu, eig_rho, s, &fallback);
     if (st0 != LRE_OK || !fallback) return st0;
@@ -478,8 +492,8 @@ lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
   const int64_t kept = hres.kept, dropped = d - kept;
   // the eigenvectors are the columns of A, ascending: kept = the last `kept`
   if (kept <= dropped)
-    return rebuild_emit(ctx, blas, C, A + (d - kept) * d, W + (d - kept), d, kept, true, res, rho_out, s);
-  return rebuild_emit(ctx, blas, C, A, W, d, dropped, false, res, rho_out, s);
+    return rebuild_emit(ctx, reinterpret_cast<cublasContext *>(blas), C, A + (d - kept) * d, W + (d - kept), d, kept, true, res, rho_out, s);
+  return rebuild_emit(ctx, reinterpret_cast<cublasContext *>(blas), C, A, W, d, dropped, false, res, rho_out, s);
 }
 
 }  // namespace lre

@@ -35,12 +35,13 @@ __device__ __forceinline__ int64_t sturm_count(const double *a, const double *b2
 
 }  // namespace
 
-// W[j] = the j-th smallest eigenvalue (j in [0, n)), one thread per
-// eigenvalue; [lo, hi) brackets every eigenvalue (Gershgorin), tol is the
-// absolute accuracy asked for.
+// W[j - j0] = the j-th smallest eigenvalue for j in [j0, j0 + cnt), one
+// thread per eigenvalue; [lo, hi) brackets every eigenvalue (Gershgorin),
+// tol is the absolute accuracy asked for.
 __global__ void tri_bisect_kernel(const double *a, const double *b2, int64_t n, double lo0, double hi0, double tol,
-                                  double pivmin, double *W) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+                                  double pivmin, double *W, int64_t j0, int64_t cnt) {
+  for (int64_t jj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jj < cnt; jj += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = j0 + jj;
     double lo = lo0, hi = hi0;  // invariant: count(lo) <= j < count(hi)
     for (int it = 0; it < 200; ++it) {
       const double mid = 0.5 * (lo + hi);
@@ -50,7 +51,7 @@ __global__ void tri_bisect_kernel(const double *a, const double *b2, int64_t n, 
       else
         hi = mid;
     }
-    W[j] = 0.5 * (lo + hi);
+    W[jj] = 0.5 * (lo + hi);
   }
 }
 

@@ -164,3 +164,37 @@ def test_batch_capture_without_uncaptured_run_is_refused(batch):
         assert err is not None and err.status == lre.LRE_ERR_UNSUPPORTED
     finally:
         lre.lre_destroy(ctx)
+
+
+def test_batch_bounded_wait_runs_out_then_context_recovers(batch):
+    """Failure detection without a fault: a test hook makes one pass of the
+    table wait for a unit that never exists, with the wait bounded at 20 ms.
+    The persistent kernel must return (every CTA leaves once the wait gives
+    up), lre_sync must report LRE_ERR_TIMEOUT, and the same context must then
+    run the batch correctly."""
+    import ctypes
+    import time
+    torch, items, host = batch
+    lre, ctx = ctx_and_lre()
+    f = lre.load().lre_debug_batch_fault
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    f.restype = ctypes.c_int
+    try:
+        assert f(ctx, 20, 1) == 0
+        t0 = time.perf_counter()
+        lre.lre_batch_run(ctx, items)
+        with pytest.raises(lre.LreError) as e:
+            lre.lre_sync(ctx)
+        assert e.value.status == lre.LRE_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 1.5        # gave up at its 20 ms bound, not the default 2 s
+        assert f(ctx, 0, -1) == 0
+        for _, _, _, theta, rho in items:
+            theta.fill_(float("nan"))
+        lre.lre_batch_run(ctx, items)
+        lre.lre_sync(ctx)
+        # the oracle reads the counts as they are now on the device (another
+        # test of this module replaces some instances' counts in place)
+        now = [(c.cpu().numpy(), shots, n) for c, shots, n, _, _ in items]
+        _check_against_single(torch, lre, ctx, items, now)
+    finally:
+        lre.lre_destroy(ctx)

@@ -2,17 +2,23 @@
 bench.py times: n = 14 GHZ + 5 % white noise, 3^14 bases x 2^14 outcomes of
 int16 counts (156.7 GB) drawn on the device, lre_estimate with the default
 (tensor-core) path.  The oracle cannot run the whole estimate, so it checks
-sampled outputs it can compute one by one: Pauli coefficients from their 3^k
-compatible bases (counts regenerated on the CPU by the same counter-based
-generator) bit for bit, rho elements from the GPU theta by the direct
-element sum (Sec. IV) within 1e-6, plus exact invariants: theta_I = 1 and a
-Hermitian rho."""
+sampled outputs it can compute one by one (tests/sampled.py): about 10^4
+Pauli coefficients stratified over k = 0..8 identity letters, from the count
+rows of their compatible bases (the rows the GPU read), bit for bit; 10^4
+rho elements (10^3 of them diagonal) by the direct element sum of Sec. IV
+from the GPU theta, each within a relative 1e-6; and exact invariants:
+theta_I = 1, a Hermitian rho of unit trace."""
 import numpy as np
 import pytest
 
+from tests import sampled
 from tests.gpu_util import ctx_and_lre, need_gpu
 
 pytestmark = pytest.mark.gpu
+
+# strings per identity count k in each block of 8 free sites (all there are
+# for k = 7, 8); seven blocks give about 10^4 strings
+QUOTA = {0: 250, 1: 250, 2: 250, 3: 250, 4: 250, 5: 150, 6: 100, 7: 24, 8: 1}
 
 
 def test_n14_headline_sampled_parity():
@@ -30,16 +36,22 @@ def test_n14_headline_sampled_parity():
         rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda")
         lre.lre_estimate(ctx, counts, wl["shots"], n, theta, rho)
         lre.lre_sync(ctx)
-        del counts
-        assert float(theta[0]) == 1.0
-        chk = bench.spot_check(torch, wl, theta, rho, n_entries=128, n_rho=64)
-        assert chk["theta_bit_exact"], chk
-        assert chk["rho_max_rel_err"] <= 1e-6, chk
-        rng = np.random.default_rng(7)
-        r = torch.from_numpy(rng.integers(0, 2 ** n, 256)).cuda()
-        c = torch.from_numpy(rng.integers(0, 2 ** n, 256)).cuda()
-        assert torch.equal(rho[r, c], torch.conj(rho[c, r]))
-        tr = torch.diagonal(rho).real.double().sum().item()
-        assert abs(tr - 1.0) < 1e-4
     finally:
-        lre.lre_destroy(ctx)
+        lre.lre_destroy(ctx)                      # frees the fold workspace
+    t_host = theta.cpu().numpy()
+    del theta
+    assert t_host[0] == 1.0
+    rng = np.random.default_rng(7)
+    rows_for = lambda b: counts[torch.from_numpy(np.asarray(b)).cuda()].cpu().numpy()
+    checked, per_k, bad = sampled.check_theta_blocks(n, t_host, wl["shots"], rows_for, rng,
+                                                     blocks=7, K=8, quota=QUOTA)
+    assert bad is None, bad
+    assert checked >= 10_000 and sorted(per_k) == list(range(9)), (checked, per_k)
+    del counts
+    rho_at = lambda r, c: rho[torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()].cpu().numpy()
+    sampled.check_rho_elements(n, t_host, rho_at, rng, count=10_000, n_diag=1_000)
+    r = torch.from_numpy(rng.integers(0, 2 ** n, 4096)).cuda()
+    c = torch.from_numpy(rng.integers(0, 2 ** n, 4096)).cuda()
+    assert torch.equal(rho[r, c], torch.conj(rho[c, r]))
+    tr = torch.diagonal(rho).real.double().sum().item()
+    assert abs(tr - 1.0) < 1e-4
