@@ -143,6 +143,29 @@ lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, c
                         int64_t shots_uniform, int n, double *theta, lre_c64 *rho,
                         lre_stream stream);
 
+/* Step (i) for one instance split over several GPUs by the axis of qubit 1
+ * (the basis groups of Sec. III partitioned by their first letter).
+ * slab: device [3^(n-1)][2^n] counts of the bases whose qubit-1 axis is one
+ * fixed a (rows a 3^(n-1) .. (a+1) 3^(n-1) - 1 of the full count matrix);
+ * row_total_bound as in lre_parity_sums.  ident: device int64 [4^(n-1)],
+ * the slab's share of the parity sums of the strings whose qubit-1 letter is
+ * I (the three slabs' shares add up to S[0 .. 4^(n-1))); own: device int64
+ * [4^(n-1)], the parity sums of the strings whose qubit-1 letter is a + 1,
+ * S[(a+1) 4^(n-1) + j], to which no other slab contributes.  Indices over
+ * qubits 2..n in Eq. (5) order.  2 <= n <= 14; exact integers whenever the
+ * bound holds.  The shares of ident are summed across GPUs by the caller
+ * (one reduce-scatter); lre_weight turns sums into theta. */
+lre_status lre_slab_sums(lre_ctx *ctx, const void *slab, lre_count_kind kind, int n, int64_t row_total_bound,
+                         int64_t *ident, int64_t *own, lre_stream stream);
+
+/* The weight of Eq. (3) with the diagonal X^T X of Sec. III on a block of
+ * exact parity sums: theta[j] = S[j] / (N 3^k), k the number of identity
+ * letters of the n-qubit Pauli index first + j, correctly rounded (the
+ * quotient lre_estimate computes).  S: device int64 [count]; theta: device
+ * FP64 [count]; shots N > 0 with N 3^n < 2^53; first + count <= 4^n. */
+lre_status lre_weight(lre_ctx *ctx, const int64_t *S, int n, int64_t first, int64_t count, int64_t shots,
+                      double *theta, lre_stream stream);
+
 /* Step (ii) alone, Eq. (4): rho = (1/2^n) sum_i theta[i] P_i, computed in
  * FP64 and rounded once to complex64.  theta: device FP64 [4^n];
  * rho: device complex64 [2^n][2^n]. */

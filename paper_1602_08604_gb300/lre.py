@@ -49,6 +49,8 @@ SIGNATURES = [
     ("lre_workspace_size", _i, [_p, _i, _i, _i, ctypes.POINTER(_sz)]),
     ("lre_parity_sums", _i, [_p, _p, _i, _i, _i64, _p, _p]),
     ("lre_estimate", _i, [_p, _p, _i, _p, _i64, _i, _p, _p, _p]),
+    ("lre_slab_sums", _i, [_p, _p, _i, _i, _i64, _p, _p, _p]),
+    ("lre_weight", _i, [_p, _p, _i, _i64, _i64, _i64, _p, _p]),
     ("lre_assemble", _i, [_p, _p, _i, _p, _p]),
     ("lre_assemble_noalloc", _i, [_p, _i, _p, _p]),
     ("lre_project", _i, [_p, _p, _i, _p, _p, _p, _p]),
@@ -164,6 +166,18 @@ def lre_estimate(ctx, counts, shots, n, theta, rho=None, stream=None, kind=None)
     k = _kind(counts) if kind is None else int(kind)
     _check(load().lre_estimate(ctx, _ptr(counts), k, sp, int(su), int(n), _ptr(theta),
                                _ptr(rho), _stream(stream)), ctx)
+
+
+def lre_slab_sums(ctx, slab, n, ident, own, row_total_bound=0, stream=None):
+    """slab: [3^(n-1)][2^n] counts of one qubit-1 axis; ident, own: int64 [4^(n-1)]."""
+    _check(load().lre_slab_sums(ctx, _ptr(slab), _kind(slab), int(n), int(row_total_bound), _ptr(ident),
+                                _ptr(own), _stream(stream)), ctx)
+
+
+def lre_weight(ctx, S, n, first, shots, theta, stream=None):
+    """theta[j] = S[j] / (N 3^k(first + j)) for the block of len(S) sums."""
+    _check(load().lre_weight(ctx, _ptr(S), int(n), int(first), int(S.numel()), int(shots), _ptr(theta),
+                             _stream(stream)), ctx)
 
 
 def lre_assemble(ctx, theta, n, rho, stream=None):

@@ -11,6 +11,14 @@ Samplers
   * ghz      (1-p)|GHZ><GHZ| + p I/d sampled directly: with probability p a
              uniform outcome, else the GHZ outcome law of basis b.
   * product  product of single-qubit states: one word per qubit and shot.
+  * mixed    the maximally mixed state I/d at any shot number, by binary
+             splitting: every qubit's outcome is a fair coin, so the shots c
+             at a node of the outcome tree (qubit 1 first) send
+             Binomial(c, 1/2) of them to bit 0, drawn exactly as the number of
+             set bits among c fair random bits (node (q, v) reads words
+             4g..4g+3 of the calls with counter (g, b, 0x44, (1 << q) | v),
+             the first c bits, word by word from the least significant bit).
+             Cost n S / 128 calls per basis instead of n S / 4.
 """
 import numpy as np
 
@@ -20,6 +28,7 @@ from .states import ternary_digits
 STREAM_CDF = 0x11
 STREAM_GHZ = 0x22
 STREAM_PROD = 0x33
+STREAM_SPLIT = 0x44
 
 
 def prob_threshold(p):
@@ -148,4 +157,56 @@ def exact_counts(probs, shots, dtype=np.int32):
     c = c.astype(np.int64)
     if np.any(c.sum(axis=1) != shots):
         raise ValueError("rounded rows do not sum to the shot count")
+    return c.astype(dtype)
+
+
+def _popcount32(x):
+    x = x.astype(np.uint64)
+    c = np.zeros(x.shape, dtype=np.int64)
+    for k in range(32):
+        c += ((x >> np.uint64(k)) & np.uint64(1)).astype(np.int64)
+    return c
+
+
+def fair_binomial(c, b, node, k0, k1):
+    """Binomial(c, 1/2) for each basis b (arrays of equal length): the number
+    of set bits among the first c bits of node `node`'s word stream."""
+    c = np.asarray(c, dtype=np.int64)
+    b = np.asarray(b, dtype=np.int64)
+    out = np.zeros(len(c), dtype=np.int64)
+    calls = (c + 127) // 128
+    for g in range(int(calls.max()) if len(c) else 0):
+        live = calls > g
+        if not np.any(live):
+            break
+        words = philox4x32(np.uint32(g), b[live], STREAM_SPLIT, np.uint32(node), k0, k1)
+        cl = c[live]
+        acc = np.zeros(int(live.sum()), dtype=np.int64)
+        for k in range(4):
+            first = 128 * g + 32 * k                  # index of this word's first bit
+            nb = np.clip(cl - first, 0, 32)           # bits of this word inside the first c
+            mask = np.where(nb >= 32, np.uint64(0xFFFFFFFF),
+                            (np.uint64(1) << nb.astype(np.uint64)) - np.uint64(1))
+            acc += _popcount32(words[k].astype(np.uint64) & mask)
+        out[live] += acc
+    return out
+
+
+def sample_mixed(n, shots, seed, bases=None, dtype=np.int32):
+    """Counts of the maximally mixed n-qubit state (every basis uniform over
+    its 2^n outcomes), drawn by binary splitting of the shots."""
+    B = 3 ** n
+    d = 1 << n
+    bases = np.arange(B, dtype=np.int64) if bases is None else np.asarray(bases, dtype=np.int64)
+    k0, k1 = seed_key(seed)
+    # slot v << (n - q) holds node (q, v): the node and its left child share a slot
+    c = np.zeros((len(bases), d), dtype=np.int64)
+    c[:, 0] = shots
+    for q in range(n):
+        half = 1 << (n - q - 1)
+        for v in range(1 << q):
+            slot = v << (n - q)
+            c0 = fair_binomial(c[:, slot], bases, (1 << q) | v, k0, k1)
+            c[:, slot + half] = c[:, slot] - c0
+            c[:, slot] = c0
     return c.astype(dtype)

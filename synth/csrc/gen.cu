@@ -23,11 +23,79 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-constexpr uint32_t STREAM_CDF = 0x11, STREAM_GHZ = 0x22, STREAM_PROD = 0x33;
+constexpr uint32_t STREAM_CDF = 0x11, STREAM_GHZ = 0x22, STREAM_PROD = 0x33, STREAM_SPLIT = 0x44;
 
 template <typename OutT>
 __device__ void write_row(const int32_t *h, OutT *row, int d) {
   for (int o = threadIdx.x; o < d; o += blockDim.x) row[o] = (OutT)h[o];
+}
+
+// Set bits among the first c bits of node `node`'s word stream for basis b,
+// calls g = g0, g0 + step, ... (Binomial(c, 1/2) summed over the caller's
+// share of the calls).
+__device__ __forceinline__ int32_t fair_bits(int32_t c, uint32_t b, uint32_t node, uint32_t k0, uint32_t k1,
+                                             int32_t g0, int32_t step) {
+  int32_t acc = 0;
+  const int32_t calls = (c + 127) >> 7;
+  for (int32_t g = g0; g < calls; g += step) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)g, b, STREAM_SPLIT, node), k0, k1);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t nb = min(max(c - (g * 128 + 32 * k), 0), 32);
+      const uint32_t mask = nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+      acc += __popc(ws[k] & mask);
+    }
+  }
+  return acc;
+}
+
+// Maximally mixed state by binary splitting of each basis' shots (qubit 1
+// first); node (q, v) lives in slot v << (n - q) of the shared array, which
+// its left child keeps: c0 = Binomial(c, 1/2) stays, c - c0 moves half a
+// subtree to the right.  Warps share a node's calls at the first six levels,
+// threads own whole nodes below.
+template <typename OutT>
+__global__ void gen_mixed_kernel(int n, int64_t b0, int64_t nb, int64_t shots, uint32_t k0, uint32_t k1,
+                                 OutT *__restrict__ counts) {
+  extern __shared__ int32_t h[];
+  const int d = 1 << n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int64_t j = blockIdx.x; j < nb; j += gridDim.x) {
+    const uint32_t b = (uint32_t)(b0 + j);
+    for (int o = threadIdx.x; o < d; o += blockDim.x) h[o] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) h[0] = (int32_t)shots;
+    __syncthreads();
+    for (int q = 0; q < n; ++q) {
+      const int half = 1 << (n - q - 1);
+      if (q < 6) {
+        for (int v = warp; v < (1 << q); v += nwarps) {
+          const int slot = v << (n - q);
+          const int32_t c = h[slot];
+          int32_t c0 = fair_bits(c, b, (1u << q) | (uint32_t)v, k0, k1, lane, 32);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+          __syncwarp();
+          if (lane == 0) {
+            h[slot] = c0;
+            h[slot + half] = c - c0;
+          }
+        }
+      } else {
+        for (int v = threadIdx.x; v < (1 << q); v += blockDim.x) {
+          const int slot = v << (n - q);
+          const int32_t c = h[slot];
+          const int32_t c0 = fair_bits(c, b, (1u << q) | (uint32_t)v, k0, k1, 0, 1);
+          h[slot] = c0;
+          h[slot + half] = c - c0;
+        }
+      }
+      __syncthreads();
+    }
+    write_row(h, counts + j * (int64_t)d, d);
+    __syncthreads();
+  }
 }
 
 template <typename OutT>
@@ -217,6 +285,20 @@ int synth_gen_product(const uint32_t *thr, int n, int64_t b0, int64_t nb, int64_
   } else {
     int smem = launch_cfg(gen_product_kernel<int32_t>, n, nb, grid);
     gen_product_kernel<int32_t><<<grid, 512, smem, s>>>(thr, n, b0, nb, shots, k0, k1, (int32_t *)counts);
+  }
+  return (int)cudaGetLastError();
+}
+
+int synth_gen_mixed(int n, int64_t b0, int64_t nb, int64_t shots, uint64_t seed, void *counts, int kind,
+                    cudaStream_t s) {
+  int grid;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if (kind == 1) {
+    int smem = launch_cfg(gen_mixed_kernel<int16_t>, n, nb, grid);
+    gen_mixed_kernel<int16_t><<<grid, 256, smem, s>>>(n, b0, nb, shots, k0, k1, (int16_t *)counts);
+  } else {
+    int smem = launch_cfg(gen_mixed_kernel<int32_t>, n, nb, grid);
+    gen_mixed_kernel<int32_t><<<grid, 256, smem, s>>>(n, b0, nb, shots, k0, k1, (int32_t *)counts);
   }
   return (int)cudaGetLastError();
 }

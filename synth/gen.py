@@ -39,7 +39,9 @@ def lib():
         L.synth_gen_ghz.argtypes = [i, u32, i64, i64, i64, u64, p, i, p]
         L.synth_gen_product.argtypes = [p, i, i64, i64, i64, u64, p, i, p]
         L.synth_gen_ghz_records.argtypes = [i, u32, i64, i64, i64, u64, p, p]
-        for f in (L.synth_gen_cdf, L.synth_gen_ghz, L.synth_gen_product, L.synth_gen_ghz_records):
+        L.synth_gen_mixed.argtypes = [i, i64, i64, i64, u64, p, i, p]
+        for f in (L.synth_gen_cdf, L.synth_gen_ghz, L.synth_gen_product, L.synth_gen_ghz_records,
+                  L.synth_gen_mixed):
             f.restype = i
         _lib = L
     return _lib
@@ -93,3 +95,11 @@ def gen_ghz_records(n, p_noise, seed, records, b0=0):
     rc = lib().synth_gen_ghz_records(n, thr, b0, nb, shots, _seed(seed), records.data_ptr(), _stream())
     if rc != 0:
         raise RuntimeError(f"synth_gen_ghz_records: cuda error {rc}")
+
+
+def gen_mixed(n, shots, seed, counts, b0=0):
+    """Maximally mixed state counts by binary splitting (synth.counts.sample_mixed)."""
+    rc = lib().synth_gen_mixed(n, b0, counts.shape[0], shots, _seed(seed), counts.data_ptr(), _kind(counts),
+                               _stream())
+    if rc != 0:
+        raise RuntimeError(f"synth_gen_mixed: cuda error {rc}")

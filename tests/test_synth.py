@@ -64,3 +64,37 @@ def test_cdf_sampler_follows_born_law_and_subsets():
     np.testing.assert_array_equal(sub, c[[3, 7]])
     sub = sc.sample_ghz(4, 0.1, 1000, seed=9, bases=[5, 80])
     np.testing.assert_array_equal(sub, sc.sample_ghz(4, 0.1, 1000, seed=9)[[5, 80]])
+
+
+def test_mixed_splitting_sampler_is_the_multinomial_of_I_over_d():
+    # rows sum to the shots exactly; every count has the Binomial(S, 1/d)
+    # mean and variance; the root split (qubit 1) is Binomial(S, 1/2);
+    # subsets of bases reproduce the full draw
+    n, S = 4, 100000
+    d = 2 ** n
+    c = sc.sample_mixed(n, S, seed=21)
+    assert np.all(c.sum(axis=1) == S)
+    x = c.astype(np.float64).ravel()
+    mean, var = S / d, S / d * (1 - 1 / d)
+    assert abs(x.mean() - mean) < 1e-9                      # the totals fix the mean exactly
+    assert abs(x.var() / var - 1) < 0.15
+    half = c[:, : d // 2].sum(axis=1).astype(np.float64)   # outcomes with o_1 = 0
+    assert abs(half.mean() - S / 2) < 4 * np.sqrt(S / 4 / len(half))
+    assert abs(half.var() / (S / 4) - 1) < 0.4
+    np.testing.assert_array_equal(sc.sample_mixed(n, S, seed=21, bases=[5, 44]), c[[5, 44]])
+
+
+def test_fair_binomial_counts_the_set_bits_of_its_stream():
+    # brute force on one node: the first c bits of the stream, one at a time
+    from synth.philox import philox4x32, seed_key
+    k0, k1 = seed_key(77)
+    for c in (1, 31, 32, 33, 127, 128, 129, 300):
+        bits = []
+        for g in range((c + 127) // 128):
+            w = philox4x32(np.uint32(g), np.uint32(9), sc.STREAM_SPLIT, np.uint32(5), k0, k1)
+            for k in range(4):
+                v = int(w[k])
+                bits.extend((v >> i) & 1 for i in range(32))
+        want = sum(bits[:c])
+        got = sc.fair_binomial(np.array([c]), np.array([9]), 5, k0, k1)[0]
+        assert got == want, (c, got, want)
