@@ -43,8 +43,9 @@
 // Range check: the encodings are exact only for counts in range, so the
 // warps that do not build or convert (RAW: warps 2, 3) read every landed
 // count, and the converter warps check what they convert; a count above the
-// stated shots per basis (or negative) latches LRE_ERR_SHOTS_MISMATCH.  The
-// MMAs of a chunk wait for that pass over it.
+// stated shots per basis (or negative) latches LRE_ERR_SHOTS_MISMATCH.  RAW:
+// the check reads a slot while its MMAs run, and the slot is released once
+// both are done; the converting variants' MMAs wait for the conversion.
 //
 // Roles (256 threads, 320 for SPLIT; one CTA per SM):
 //   warp 0     TMA producer into a ring of 3 chunk slots (RAW/BIASED: one
@@ -153,7 +154,9 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     for (int i = 0; i < MMA_R; ++i) {
       sm103::mbar_init(&full[i], 1);
       sm103::mbar_init(&conv[i], 32 * MmaCfg<V>::CONV_WARPS);
-      sm103::mbar_init(&empty[i], 1);
+      // RAW: released by the MMAs' commit and by the two range-check warps,
+      // which read the slot while the MMAs run
+      sm103::mbar_init(&empty[i], V == V_RAW ? 3 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       sm103::mbar_init(&tile_done[b], 1);
@@ -278,7 +281,8 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         give_up();
         break;
       }
-      if (!sm103::mbar_wait(RECORDS ? &full[slot] : &conv[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+      if (!sm103::mbar_wait((RECORDS || V == V_RAW) ? &full[slot] : &conv[slot], (uint32_t)((g / MMA_R) & 1),
+                            abort_flag)) {
         give_up();
         break;
       }
@@ -372,8 +376,13 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
           }
         }
       }
-      if (BIASED || SPLIT) sm103::fence_proxy_async_smem();
-      sm103::mbar_arrive(&conv[slot]);
+      if constexpr (V == V_RAW) {  // done reading: one arrival per warp on the slot's release
+        __syncwarp();
+        if (lane == 0) sm103::mbar_arrive(&empty[slot]);
+      } else {
+        sm103::fence_proxy_async_smem();
+        sm103::mbar_arrive(&conv[slot]);
+      }
     }
     // a count above the shots per basis (a negative one reads as a large
     // unsigned value) is outside the encoding's exact range

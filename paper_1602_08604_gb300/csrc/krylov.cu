@@ -567,9 +567,14 @@ lre_status project_krylov(lre_ctx *ctx, cublasContext *blas, const lre_c64 *rho_
     if (r >= 0) break;
     if (r_top >= 0 || r_bot >= 0) return LRE_OK;  // decided, but too many vectors: reduction path
     if (broke) return LRE_OK;  // exact but undecided: reduction path
-    // widen an end whose values all converged without deciding
-    if (top_open && r_top < 0 && CT == ct_want) ct_want = (int)std::min<int64_t>(2 * ct_want, B.ct_max - cb_want);
-    if (bot_open && r_bot < 0 && CB == cb_want) cb_want = (int)std::min<int64_t>(2 * cb_want, 256);
+    // widen an end whose values all converged without deciding; when both
+    // ends are at their widest and still undecided, both sets are too large
+    const bool top_full = top_open && r_top < 0 && CT == ct_want;
+    const bool bot_full = bot_open && r_bot < 0 && CB == cb_want;
+    const int ct_cap = (int)(B.ct_max - 256), cb_cap = 256;
+    if (top_full && bot_full && ct_want >= ct_cap && cb_want >= cb_cap) return LRE_OK;  // reduction path
+    if (top_full) ct_want = std::min(2 * ct_want, ct_cap);
+    if (bot_full) cb_want = std::min(2 * cb_want, cb_cap);
   }
   if (r < 0) return LRE_OK;  // undecided within the step limit: reduction path
 
