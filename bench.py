@@ -380,7 +380,8 @@ def arm_record(lre, torch, device, stream, counts, wl, workload, path, steps, wa
     n = wl["n"]
     ctx = lre.lre_create(device.index)
     try:
-        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if path == "tensor" else lre.LRE_FOLD_FWHT)
+        lre.lre_set_fold_path(ctx, {"tensor": lre.LRE_FOLD_TENSOR, "tensor_split": lre.LRE_FOLD_TENSOR_SPLIT,
+                                    "fwht": lre.LRE_FOLD_FWHT}[path])
         theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
         rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
         total_ms, recs, launches = timed_steps(
@@ -401,6 +402,62 @@ def arm_record(lre, torch, device, stream, counts, wl, workload, path, steps, wa
     return out, theta
 
 
+def fused_generation_arm(lre, torch, device, stream, wl, theta_ref, steps, warmup, chunk_rows=4 * 729):
+    """Generation fused with the fold: the device generator fills one slot of
+    a two-slot ring of count chunks (whole tile rows), lre_stream_chunk folds
+    it at once, so the count matrix never exists; a step is generation plus
+    estimate.  Beside it, the materialised path's generation of the whole
+    matrix, timed the same way (the headline step then adds its ms)."""
+    from synth import gen
+    n, N = wl["n"], wl["shots"]
+    B, d = 3 ** n, 2 ** n
+    ring = [torch.empty((chunk_rows, d), dtype=torch.int16, device=device) for _ in range(2)]
+    theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
+    rho = torch.empty((d, d), dtype=torch.complex64, device=device)
+    ctx = lre.lre_create(device.index)
+    try:
+        def step():
+            lre.lre_stream_begin(ctx, n, lre.LRE_COUNTS_I16, N)
+            for k, b0 in enumerate(range(0, B, chunk_rows)):
+                buf = ring[k % 2][: min(chunk_rows, B - b0)]
+                gen.gen_ghz(n, wl["p"], N, wl["seed"], buf, b0=b0)
+                lre.lre_stream_chunk(ctx, buf, b0, stream=stream)
+            lre.lre_stream_end(ctx, theta, rho, stream=stream)
+
+        total_ms, recs, launches = timed_steps(lre, ctx, torch, stream, step, steps, warmup)
+    finally:
+        lre.lre_destroy(ctx)
+    ms = total_ms / steps
+    same = bool(torch.equal(theta, theta_ref))
+    del theta, rho, ring
+    torch.cuda.empty_cache()
+    # the materialised path's generation of the whole matrix, same events
+    full = torch.empty((B, d), dtype=torch.int16, device=device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    gen.gen_ghz(n, wl["p"], N, wl["seed"], full)
+    e0.record(stream)
+    gen.gen_ghz(n, wl["p"], N, wl["seed"], full)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gen_ms = e0.elapsed_time(e1)
+    del full
+    torch.cuda.empty_cache()
+    per = {}
+    for name, t in recs:
+        per[name] = per.get(name, 0.0) + t
+    lre_ms = sum(per.values()) / steps
+    return {"ms_per_step": round(ms, 3), "value": round(B / (ms / 1e3), 1), "unit": "Pauli bases/s",
+            "steps": steps, "warmup": warmup, "chunk_bases": chunk_rows,
+            "count_buffer_bytes": 2 * chunk_rows * d * 2, "library_kernels_ms_per_step": round(lre_ms, 3),
+            "generator_and_gaps_ms_per_step": round(ms - lre_ms, 3), "gpu_launches": launches,
+            "materialised_generation_ms": round(gen_ms, 3),
+            "theta_equal_to_headline_arm": same,
+            "note": "a step generates the counts (GHZ sampler, device) and estimates theta and rho; the "
+                    "materialised path needs the 156.7 GB count matrix, generated in "
+                    "materialised_generation_ms, before its step"}
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -415,7 +472,8 @@ def run_ours(args, wl):
     theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
     rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device=device)
     ctx = lre.lre_create(local)
-    lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if args.fold_path == "tensor" else lre.LRE_FOLD_FWHT)
+    lre.lre_set_fold_path(ctx, {"tensor": lre.LRE_FOLD_TENSOR, "tensor_split": lre.LRE_FOLD_TENSOR_SPLIT,
+                                "fwht": lre.LRE_FOLD_FWHT}[args.fold_path])
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -445,7 +503,7 @@ def run_ours(args, wl):
     if args.compare and rank == 0 and world == 1:
         # the other first-pass arm on the same resident counts (spec:
         # tensor-core form against the plain FWHT path, same accuracy)
-        other = "fwht" if args.fold_path == "tensor" else "tensor"
+        other = "fwht" if args.fold_path != "fwht" else "tensor"
         compare[f"{args.workload}_{other}"], _ = arm_record(
             lre, torch, device, stream, counts, wl, args.workload, other, args.compare_steps, 2, theta_ref=theta)
         torch.cuda.empty_cache()
@@ -513,17 +571,21 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         e2e = run_e2e(args, wl, lre, torch, device, theta_keep)
-        del theta_keep
     else:
+        theta_keep = theta
         del counts, rho
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     if args.compare and rank == 0 and world == 1 and args.workload == "n14":
+        compare["n14_fused_generation"] = fused_generation_arm(lre, torch, device, stream, wl, theta_ref=theta_keep,
+                                                               steps=2, warmup=1)
+        del theta_keep
+        torch.cuda.empty_cache()
         # the int32 precision workload (n = 12, 4096 shots per basis): the
         # tensor-core form (two fp16 planes per count) against the FWHT path
         wl12 = WORKLOADS["n12"]
         c12 = make_counts(torch, wl12, device)
-        rec_t, th_t = arm_record(lre, torch, device, stream, c12, wl12, "n12", "tensor", args.compare_steps, 3)
+        rec_t, th_t = arm_record(lre, torch, device, stream, c12, wl12, "n12", "tensor_split", args.compare_steps, 3)
         rec_f, _ = arm_record(lre, torch, device, stream, c12, wl12, "n12", "fwht", args.compare_steps, 3,
                               theta_ref=th_t)
         compare["n12_tensor"], compare["n12_fwht"] = rec_t, rec_f
@@ -792,8 +854,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-project", dest="project", action="store_false",
                     help="skip the one timed run of step (iii) (the projection)")
-    ap.add_argument("--fold-path", default="tensor", choices=["fwht", "tensor"],
-                    help="first fold pass on the tensor cores (the library default) or on the ALUs (FWHT)")
+    ap.add_argument("--fold-path", default="tensor", choices=["fwht", "tensor", "tensor_split"],
+                    help="first fold pass on the tensor cores (the library default: int16 counts), also for "
+                         "int32 counts as two fp16 planes (tensor_split), or on the ALUs (FWHT)")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the comparison arms (the other first-pass path on the same counts; for the "
                          "n=14 workload also the n=12 int32 workload on both paths and the batched launch)")

@@ -166,6 +166,21 @@ lre_status lre_slab_sums(lre_ctx *ctx, const void *slab, lre_count_kind kind, in
 lre_status lre_weight(lre_ctx *ctx, const int64_t *S, int n, int64_t first, int64_t count, int64_t shots,
                       double *theta, lre_stream stream);
 
+/* Steps (i)+(ii) with 4^n measurement operators instead of 6^n (Sec. VI,
+ * which states the cost drop to O(8^n) but names no operator set; read as
+ * the minimal informationally complete subset of the Pauli eigenprojectors,
+ * |0>, |1>, |+>, |+i> per qubit).  Their frequencies come from the same Pauli
+ * counts -- |0>, |1> from the Z basis, |+> and |+i> from outcome 0 of the X
+ * and Y bases -- so counts, kind and shots_uniform are as for lre_estimate
+ * (uniform shots N; N 3^n < 2^53).  Eq. (3) with these 4^n rows (X square
+ * and invertible, X^T X = G^{(x)n} not diagonal) is exact: per qubit
+ * <I> = p_0 + p_1, <X> = 2p_+ - p_0 - p_1, <Y> = 2p_+i - p_0 - p_1,
+ * <Z> = p_0 - p_1; theta (same units and order as lre_estimate) is one
+ * correctly rounded division of exact integer sums by N.  rho (or NULL) as
+ * lre_assemble.  Only the 4^n used counts are read. */
+lre_status lre_estimate_ic4(lre_ctx *ctx, const void *counts, lre_count_kind kind, int64_t shots_uniform, int n,
+                            double *theta, lre_c64 *rho, lre_stream stream);
+
 /* Step (ii) alone, Eq. (4): rho = (1/2^n) sum_i theta[i] P_i, computed in
  * FP64 and rounded once to complex64.  theta: device FP64 [4^n];
  * rho: device complex64 [2^n][2^n]. */
@@ -278,12 +293,50 @@ lre_status lre_batch_schedule(const lre_ctx *ctx, int *jmax, int *ctas_per_sm, i
  *   sum stays below 2^24 units, so the result is bit-identical to the FWHT
  *   path.  It applies to int16 counts whose per-basis shot number (hence
  *   every count) is at most 2047, with uniform shots; every other call runs
- *   the FWHT path.
+ *   the FWHT path.  Every count is checked (see lre_estimate).
+ * LRE_FOLD_TENSOR_SPLIT: as LRE_FOLD_TENSOR, and int32 counts with at most
+ *   16383 shots per basis on the tensor cores too, each count split into two
+ *   fp16 planes (c mod 2048 and (c >> 11) 2^11) contracted in one MMA chain;
+ *   bit-identical, but slower than the FWHT path on GB300 (the in-place
+ *   conversion holds each shared-memory slot longer), hence not the default.
  * LRE_FOLD_FWHT: the parity transform (Walsh-Hadamard butterflies) and the
  *   ternary fold on the integer ALUs, for every input. */
 #define LRE_FOLD_FWHT 0
 #define LRE_FOLD_TENSOR 1
+#define LRE_FOLD_TENSOR_SPLIT 2
 lre_status lre_set_fold_path(lre_ctx *ctx, int path);
+
+/* Steps (i)+(ii) on counts that arrive in chunks (Sec. III's per-group
+ * results produced or received over time), so the whole [3^n][2^n] matrix
+ * never has to exist on the device: each chunk of whole tile rows (729
+ * consecutive bases) goes through the six-qubit first fold pass at once and
+ * only its partial sums are kept; lre_stream_end runs the other passes and
+ * the assembly.  Results are bit-identical to lre_estimate with uniform shots
+ * on the whole matrix.  7 <= n <= 14.
+ * lre_stream_begin: start an instance (kind int16/int32, shots per basis N);
+ *   sizes the workspace (first-pass partials, later passes, T).
+ * lre_stream_chunk: counts device [num_bases][2^n] of `kind`, 16-byte
+ *   aligned, holding bases first_basis .. first_basis + num_bases - 1;
+ *   chunks come in order (first_basis = the bases done so far), both numbers
+ *   multiples of 729.  The chunk may be reused as soon as the stream has
+ *   passed this call's work.
+ * lre_stream_end: once all 3^n bases are in; theta device FP64 [4^n], rho
+ *   device complex64 [2^n][2^n] or NULL, as lre_estimate (including the
+ *   latched LRE_ERR_SHOTS_MISMATCH on a wrong grand total).
+ * lre_stream_checkpoint: copy the state (a header and the partial sums of the
+ *   bases done, 3 or 4 bytes per partial) into host memory: *needed receives
+ *   its size; host NULL only queries it; synchronises `stream`.
+ * lre_stream_resume: restore a checkpoint into this (for instance a new)
+ *   context; the next chunk starts at the checkpoint's bases done.
+ * No other call may use the context between begin and end (they share its
+ * workspace); a call that reallocates it makes the stream calls return
+ * LRE_ERR_INVALID_ARG. */
+lre_status lre_stream_begin(lre_ctx *ctx, int n, lre_count_kind kind, int64_t shots_uniform);
+lre_status lre_stream_chunk(lre_ctx *ctx, const void *counts, int64_t first_basis, int64_t num_bases,
+                            lre_stream stream);
+lre_status lre_stream_end(lre_ctx *ctx, double *theta, lre_c64 *rho, lre_stream stream);
+lre_status lre_stream_checkpoint(lre_ctx *ctx, void *host, size_t bytes, size_t *needed, lre_stream stream);
+lre_status lre_stream_resume(lre_ctx *ctx, const void *host, size_t bytes, lre_stream stream);
 
 /* Synchronise `stream` and return (and clear) the first error latched by a
  * kernel since the last lre_sync. */

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblre.so")
-SOURCES = ["abi.cu", "fold.cu", "assemble.cu", "project.cu", "host.cu", "noalloc.cu", "batch.cu", "fold_mma.cu", "fold_tma.cu", "tridiag.cu", "records.cu", "krylov.cu", "slab.cu"]
+SOURCES = ["abi.cu", "fold.cu", "assemble.cu", "project.cu", "host.cu", "noalloc.cu", "batch.cu", "fold_mma.cu", "fold_tma.cu", "tridiag.cu", "records.cu", "krylov.cu", "slab.cu", "ic4.cu", "stream.cu"]
 HEADERS = [os.path.join(CSRC, "lre_internal.cuh"), os.path.join(CSRC, "sm103.cuh"),
            os.path.join(CSRC, "passes.cuh"),
            os.path.join(ROOT, "include", "lre.h")]

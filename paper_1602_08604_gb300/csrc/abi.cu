@@ -503,7 +503,8 @@ extern "C" lre_status lre_batch_schedule(const lre_ctx *ctx, int *jmax, int *cta
 }
 
 extern "C" lre_status lre_set_fold_path(lre_ctx *ctx, int path) {
-  if (!ctx || (path != LRE_FOLD_FWHT && path != LRE_FOLD_TENSOR)) return LRE_ERR_INVALID_ARG;
+  if (!ctx || (path != LRE_FOLD_FWHT && path != LRE_FOLD_TENSOR && path != LRE_FOLD_TENSOR_SPLIT))
+    return LRE_ERR_INVALID_ARG;
   ctx->fold_path = path;
   return LRE_OK;
 }

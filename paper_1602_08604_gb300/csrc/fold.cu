@@ -690,15 +690,24 @@ namespace {
 // Operand variant of the tensor-core first pass for this pass (0 raw int16,
 // 1 biased int16, 3 int32 in two planes), or -1 when the ALU pass runs.
 int tensor_variant(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
-  if (!pp.first6 || pp.fused9 || ctx->fold_path != 1 || !ctx->mma_operand || a.shots != nullptr ||
+  if (!pp.first6 || pp.fused9 || ctx->fold_path < 1 || !ctx->mma_operand || a.shots != nullptr ||
       a.shots_uniform <= 0)
     return -1;
-  const int v = pp.in_t == T_I16 ? ctx->mma_biased : (pp.in_t == T_I32 ? 3 : -1);
+  const int v = pp.in_t == T_I16 ? ctx->mma_biased : (pp.in_t == T_I32 && ctx->fold_path == 2 ? 3 : -1);
   return v >= 0 && a.shots_uniform <= mma_max_count(v) ? v : -1;
 }
 
 bool tensor_first_pass(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
   return tensor_variant(ctx, pp, a) >= 0;
+}
+
+// The tensor-core first pass writes its partials (below 729 x shots, which
+// must stay below 2^23) as split planes (3 bytes instead of 4) when the next
+// pass is a TMA-staged store pass that reads them back.
+bool use_planes(lre_ctx *ctx, const std::vector<PassPlan> &plan, const FoldArgs &a) {
+  return !plan.empty() && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
+         a.shots_uniform * 729 < (1ll << 23) && plan[1].mode == M_STORE && plan[1].in_t == T_I32 &&
+         ctx->generic_tma && plan[1].C % 32 == 0;
 }
 
 }  // namespace
@@ -710,6 +719,15 @@ int64_t fold_split_rows(lre_ctx *ctx, const FoldArgs &a) {
   if (plan.empty() || !plan[0].first6 || plan[0].fused9) return 0;
   // the tensor-core and TMA-pipeline kernels take tile ranges; the register kernel does not
   return (tensor_first_pass(ctx, plan[0], a) || ctx->first_variant >= 1) ? 729 : 0;
+}
+
+bool fold_stage1_layout(lre_ctx *ctx, const FoldArgs &a, bool *planes, int64_t *elems) {
+  if (a.shots || fold_split_rows(ctx, a) == 0) return false;
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(a.counts) & 15) == 0;
+  auto plan = make_plan(a.n, a.kind, false, a.S != nullptr, a.shots_uniform, aligned16, ctx->first_variant);
+  *elems = ipow(6, plan[0].r - 6) * 4096;
+  *planes = use_planes(ctx, plan, a);
+  return true;
 }
 
 bool fold_first_is_tensor(lre_ctx *ctx, const FoldArgs &a) {
@@ -742,12 +760,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
     Launch L(ctx, "inv_shots", s);
     inv_shots_kernel<<<256, 256, 0, s>>>(a.shots, wgt, B, ctx->d_status);
   }
-  // The tensor-core first pass writes its partials (below 729 x shots, which
-  // must stay below 2^23) as split planes (3 bytes instead of 4) when the
-  // next pass is a TMA-staged store pass that reads them back.
-  const bool planes = !plan.empty() && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
-                      a.shots_uniform * 729 < (1ll << 23) && plan[1].mode == M_STORE && plan[1].in_t == T_I32 &&
-                      ctx->generic_tma && plan[1].C % 32 == 0;
+  const bool planes = use_planes(ctx, plan, a);
   const void *in = a.counts;
   size_t k_begin = 0, k_end = plan.size();
   if (a.stage != 0) {
@@ -782,18 +795,22 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       if (st != LRE_OK) return st;
     } else if (tensor) {
       const lre_count_kind mk = pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32;
-      if (!make_count_map(&tmap, in, mk, pp.r, ipow(3, pp.r), mma_box_rows(0)) ||
-          !make_count_map(&tmap_tail, in, mk, pp.r, ipow(3, pp.r), mma_box_rows(1))) {
+      const int64_t rows = (a.stage == 1 && a.rows_in > 0) ? a.rows_in : ipow(3, pp.r);
+      const int tv = tensor_variant(ctx, pp, a);
+      if (!make_count_map(&tmap, in, mk, pp.r, rows, mma_box_rows(0, tv)) ||
+          !make_count_map(&tmap_tail, in, mk, pp.r, rows, mma_box_rows(1, tv))) {
         ctx->last_error = "tensor map of the counts rejected";
         return LRE_ERR_CUDA;
       }
       const int64_t elems = ipow(6, pp.r - 6) * 4096;
       int8_t *hi = planes ? static_cast<int8_t *>(out) + elems * 2 : nullptr;
       lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), hi,
-                                     pp.r, tensor_variant(ctx, pp, a), a.shots_uniform, tile_begin, tile_end, s);
+                                     pp.r, tensor_variant(ctx, pp, a), a.shots_uniform, tile_begin, tile_end,
+                                     a.stage == 1 ? a.row_base : 0, s);
       if (st != LRE_OK) return st;
     } else if (pp.first6 && (ctx->first_variant >= 1 || pp.fused9) &&
-        make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r, ipow(3, pp.r))) {
+        make_count_map(&tmap, in, pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32, pp.r,
+                       (a.stage == 1 && a.rows_in > 0) ? a.rows_in : ipow(3, pp.r))) {
       const int64_t tiles = tile_end - tile_begin;
       int grid = ctx->num_sms;
       if ((int64_t)grid > tiles) grid = (int)tiles;
@@ -802,7 +819,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       A.n = pp.r;
       A.tile_begin = tile_begin;
       A.tile_end = tile_end;
-      A.row_base = 0;
+      A.row_base = a.stage == 1 ? a.row_base : 0;
       A.status = ctx->d_status;
       A.fuse = pp.fused9 ? 1 : 0;
       const int threads = pp.fused9 ? FUSE_THREADS : PIPE_THREADS;

@@ -85,18 +85,26 @@ constexpr int MMA_THREADS = 256;
 constexpr int MMA_R = 3;                       // ring slots of one chunk each
 constexpr int CHUNK_ROWS = 432;                // 16 alB groups x 27 rows
 constexpr int SLOT_BYTES = CHUNK_ROWS * 128;   // int16 rows of 64 outcomes
-constexpr int SPLIT_ROWS = 216;                // SPLIT: 8 alB groups x 27 int32 rows
-constexpr int SPLIT_TAIL = 81;                 // SPLIT: the last chunk, alB 24..26
+// SPLIT chunks: 8 alB groups (216 int32 rows, N = 64) three times, then alB
+// 24..26 (81 rows, N = 32, whose padded alB = 27 reads rows 81..107).
+// Measured: 216-row chunks in 3 slots (2.70 ms at n = 12) beat 108-row
+// chunks in 6 slots (3.64 ms): the per-chunk fixed costs outweigh the
+// extra loads in flight.
+constexpr int SPLIT_ROWS = 216;
+constexpr int SPLIT_TAIL = 81;
+constexpr int SPLIT_CHUNKS = 4;                // 3 x 216 + 81 = 729 rows
 constexpr int64_t SPLIT_MAX = 16383;           // SPLIT: largest count (216 c < 2^22)
+static_assert(3 * SPLIT_ROWS + SPLIT_TAIL == 729, "chunks cover the tile");
 static_assert(SPLIT_ROWS * 256 == SLOT_BYTES, "a SPLIT chunk fills one slot");
-// the last SPLIT chain (N = 32) reads alB = 27 (rows 81..107 of its chunk)
 static_assert(4 * 27 <= SPLIT_ROWS, "padded alB group stays in the slot");
 
 template <int V>
 struct MmaCfg {
-  static constexpr int CPT = V == V_SPLIT ? 4 : 2;           // chunks per tile
-  static constexpr int THREADS = V == V_SPLIT ? 320 : 256;   // + warps 8, 9 convert
-  static constexpr int CONV_WARPS = V == V_SPLIT ? 4 : 2;    // arrivals on conv: 32 each
+  static constexpr int CPT = V == V_SPLIT ? SPLIT_CHUNKS : 2;       // chunks per tile
+  static constexpr int R = MMA_R;                                     // ring slots
+  static constexpr int SLOT = SLOT_BYTES;
+  static constexpr int THREADS = V == V_SPLIT ? 320 : 256;           // + warps 8, 9 convert
+  static constexpr int CONV_WARPS = V == V_SPLIT ? 4 : 2;            // arrivals on conv: 32 each
 };
 constexpr int A_BYTES = 16 * 28 * 128;         // 128 x 224 fp16, core-matrix layout
 constexpr int OFF_RING = A_BYTES;
@@ -132,17 +140,19 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
                     const uint4 *__restrict__ gA, int32_t *__restrict__ out, int8_t *__restrict__ out_hi, int n,
                     int64_t tile_begin, int64_t tile_end, const uint16_t *__restrict__ entries,
-                    const int32_t *__restrict__ offs, int64_t shots, int *status) {
+                    const int32_t *__restrict__ offs, int64_t shots, int64_t row_base, int *status) {
   constexpr bool BIASED = V == V_BIASED, RECORDS = V == V_RECORDS, SPLIT = V == V_SPLIT;
   constexpr int CPT = MmaCfg<V>::CPT;
+  constexpr int MR = MmaCfg<V>::R;          // ring slots
+  constexpr int SLOT = MmaCfg<V>::SLOT;     // bytes per slot
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (sm103::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *Am = smem;
   uint8_t *ring = smem + OFF_RING;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + OFF_BAR);
-  uint64_t *conv = full + MMA_R;
-  uint64_t *empty = conv + MMA_R;
-  uint64_t *tile_done = empty + MMA_R;
+  uint64_t *conv = full + MR;
+  uint64_t *empty = conv + MR;
+  uint64_t *tile_done = empty + MR;
   uint64_t *tile_free = tile_done + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tile_free + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -151,7 +161,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
 
   for (int i = threadIdx.x; i < A_BYTES / 16; i += MmaCfg<V>::THREADS) reinterpret_cast<uint4 *>(Am)[i] = gA[i];
   if (threadIdx.x == 0) {
-    for (int i = 0; i < MMA_R; ++i) {
+    for (int i = 0; i < MR; ++i) {
       sm103::mbar_init(&full[i], 1);
       sm103::mbar_init(&conv[i], 32 * MmaCfg<V>::CONV_WARPS);
       // RAW: released by the MMAs' commit and by the two range-check warps,
@@ -186,16 +196,16 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     const int64_t row_entries = 729 * shots;
     const int nb = (int)(2 * n_oh);  // buckets per tile row: (oh, chunk)
     constexpr int32_t SPARSE = 2048;  // re-zero only the touched cells below this many entries
-    uint4 *slot4 = reinterpret_cast<uint4 *>(ring + bw * SLOT_BYTES);
-    uint32_t *slot32 = reinterpret_cast<uint32_t *>(ring + bw * SLOT_BYTES);
+    uint4 *slot4 = reinterpret_cast<uint4 *>(ring + bw * SLOT);
+    uint32_t *slot32 = reinterpret_cast<uint32_t *>(ring + bw * SLOT);
     const uint16_t *pent = nullptr;  // the slot's previous chunk: its entries and row base
     int32_t pe0 = 0, pe1 = -1;
     int pbase = 0;
-    for (int64_t g = bw; g < total; g += MMA_R) {
+    for (int64_t g = bw; g < total; g += MR) {
       const int64_t tile = tile_begin + blockIdx.x + (g >> 1) * gridDim.x;
       const int c = (int)(g & 1);
       const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
-      if (g >= MMA_R && !sm103::mbar_wait(&empty[bw], (uint32_t)((g / MMA_R - 1) & 1), abort_flag)) {
+      if (g >= MR && !sm103::mbar_wait(&empty[bw], (uint32_t)((g / MR - 1) & 1), abort_flag)) {
         give_up();
         break;
       }
@@ -243,19 +253,19 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         const int64_t tile = tile_begin + blockIdx.x + (g / CPT) * gridDim.x;
         const int c = (int)(g % CPT);
         const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
-        const int slot = (int)(g % MMA_R);
-        if (g >= MMA_R && !sm103::mbar_wait(&empty[slot], (uint32_t)((g / MMA_R - 1) & 1), abort_flag)) {
+        const int slot = (int)(g % MR);
+        if (g >= MR && !sm103::mbar_wait(&empty[slot], (uint32_t)((g / MR - 1) & 1), abort_flag)) {
           give_up();
           break;
         }
-        uint8_t *dst = ring + slot * SLOT_BYTES;
+        uint8_t *dst = ring + slot * SLOT;
         const int x = (int)(oh * 64);
         if constexpr (SPLIT) {  // one box of int32 rows: 216, or 81 for alB 24..26
-          const int y = (int)(ah * 729 + c * SPLIT_ROWS);
-          sm103::mbar_arrive_expect_tx(&full[slot], (c < 3 ? SPLIT_ROWS : SPLIT_TAIL) * 256);
-          sm103::tma_load_2d(dst, c < 3 ? &map_big : &map_tail, x, y, &full[slot]);
+          const int y = (int)(ah * 729 + c * SPLIT_ROWS - row_base);
+          sm103::mbar_arrive_expect_tx(&full[slot], (c < SPLIT_CHUNKS - 1 ? SPLIT_ROWS : SPLIT_TAIL) * 256);
+          sm103::tma_load_2d(dst, c < SPLIT_CHUNKS - 1 ? &map_big : &map_tail, x, y, &full[slot]);
         } else {
-          const int y = (int)(ah * 729 + c * 432);
+          const int y = (int)(ah * 729 + c * 432 - row_base);
           sm103::mbar_arrive_expect_tx(&full[slot], (BOX_BIG + (c ? BOX_TAIL : BOX_BIG)) * 128);
           sm103::tma_load_2d(dst, &map_big, x, y, &full[slot]);
           if (c == 0)
@@ -264,15 +274,15 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
             sm103::tma_load_2d(dst + BOX_BIG * 128, &map_tail, x, y + (int)BOX_BIG, &full[slot]);
         }
       }
-      for (int64_t q = g > MMA_R ? g - MMA_R : 0; q < g; ++q)  // drain in-flight loads
+      for (int64_t q = g > MR ? g - MR : 0; q < g; ++q)  // drain in-flight loads
         for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
-          if (sm103::mbar_try_wait(&full[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
+          if (sm103::mbar_try_wait(&full[q % MR], (uint32_t)((q / MR) & 1))) break;
     }
   } else if (warp == 1) {
     const uint32_t a_base = sm103::smem_addr(Am);
     int64_t g = 0;
     for (; g < total; ++g) {
-      const int slot = (int)(g % MMA_R);
+      const int slot = (int)(g % MR);
       const int64_t lt = g / CPT;
       const int c = (int)(g % CPT);
       const int tb = (int)(lt & 1);
@@ -281,17 +291,17 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         give_up();
         break;
       }
-      if (!sm103::mbar_wait((RECORDS || V == V_RAW) ? &full[slot] : &conv[slot], (uint32_t)((g / MMA_R) & 1),
+      if (!sm103::mbar_wait((RECORDS || V == V_RAW) ? &full[slot] : &conv[slot], (uint32_t)((g / MR) & 1),
                             abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
       if (lane == 0) {
-        const uint32_t b_base = sm103::smem_addr(ring + slot * SLOT_BYTES);
+        const uint32_t b_base = sm103::smem_addr(ring + slot * SLOT);
         if constexpr (SPLIT) {
           const uint32_t d = tmem + tb * TILE_COLS + c * 64;
-          const uint32_t idesc = sm103::umma_idesc_f16(128, c < 3 ? 64 : 32);
+          const uint32_t idesc = sm103::umma_idesc_f16(128, c < SPLIT_CHUNKS - 1 ? 64 : 32);
 #pragma unroll 1
           for (int kk = 0; kk < 14; ++kk) {
             const int brow = kk < 13 ? 2 * kk : 25;
@@ -322,21 +332,21 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     if (lane == 0 && g > 0) {
       const int64_t q = g - 1;
       for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)
-        if (sm103::mbar_try_wait(&empty[q % MMA_R], (uint32_t)((q / MMA_R) & 1))) break;
+        if (sm103::mbar_try_wait(&empty[q % MR], (uint32_t)((q / MR) & 1))) break;
     }
   } else if (conv_warp) {
     // range check of every landed count (and the BIASED / SPLIT conversion)
     uint32_t mx = 0;  // SPLIT: largest count as unsigned; else the two 16-bit halves' maxima
     for (int64_t g = 0; g < total; ++g) {
-      const int slot = (int)(g % MMA_R);
+      const int slot = (int)(g % MR);
       const int c = (int)(g % CPT);
-      if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MMA_R) & 1), abort_flag)) {
+      if (!sm103::mbar_wait(&full[slot], (uint32_t)((g / MR) & 1), abort_flag)) {
         give_up();
         break;
       }
-      uint8_t *base = ring + slot * SLOT_BYTES;
+      uint8_t *base = ring + slot * SLOT;
       if constexpr (SPLIT) {
-        const int rows = c < 3 ? SPLIT_ROWS : SPLIT_TAIL;
+        const int rows = c < SPLIT_CHUNKS - 1 ? SPLIT_ROWS : SPLIT_TAIL;
         const int cw = warp < 4 ? warp - 2 : warp - 6;  // 0..3
         const int q = lane & 15;                        // 16 bytes (4 counts) of a 256-byte row
         for (int r0 = 2 * cw; r0 < rows; r0 += 8) {    // two rows per warp at a time
@@ -481,7 +491,10 @@ std::vector<uint16_t> make_a_operand() {
 }  // namespace
 
 size_t mma_operand_bytes() { return A_BYTES; }
-uint32_t mma_box_rows(int which) { return which ? BOX_TAIL : BOX_BIG; }
+uint32_t mma_box_rows(int which, int variant) {
+  if (variant == 3) return which ? SPLIT_TAIL : SPLIT_ROWS;
+  return which ? BOX_TAIL : BOX_BIG;
+}
 int64_t mma_max_count(int variant) { return variant == 1 ? 1023 : (variant == 3 ? SPLIT_MAX : 2047); }
 
 // Launch the tensor-core first pass over tiles [tile_begin, tile_end) of an
@@ -491,12 +504,12 @@ int64_t mma_max_count(int variant) { return variant == 1 ? 1023 : (variant == 3 
 // uint16) and the bits above at out_hi (int8), exact while every partial is
 // below 2^23 in magnitude (729 x shots).  map_big / map_tail are tensor maps
 // of the counts (int16, or int32 for SPLIT) with boxes of 216 / 81 rows x 64
-// outcomes; a_dev holds the operand written by mma_operand_upload; shots is
-// the shots per basis, at most mma_max_count(variant): a count above it
-// latches LRE_ERR_SHOTS_MISMATCH.
+// outcomes, whose row 0 is basis row_base; a_dev holds the operand written by
+// mma_operand_upload; shots is the shots per basis, at most
+// mma_max_count(variant): a count above it latches LRE_ERR_SHOTS_MISMATCH.
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
                           int32_t *out, int8_t *out_hi, int n, int variant, int64_t shots, int64_t tile_begin,
-                          int64_t tile_end, cudaStream_t s) {
+                          int64_t tile_end, int64_t row_base, cudaStream_t s) {
   const int64_t tiles = tile_end - tile_begin;
   if (tiles <= 0) return LRE_OK;
   if (shots <= 0 || shots > mma_max_count(variant) || (variant != 0 && variant != 1 && variant != 3))
@@ -508,7 +521,7 @@ lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtens
   const int threads = variant == 3 ? MmaCfg<V_SPLIT>::THREADS : MMA_THREADS;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
   kern<<<grid, threads, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, out_hi, n,
-                                       tile_begin, tile_end, nullptr, nullptr, shots, ctx->d_status);
+                                       tile_begin, tile_end, nullptr, nullptr, shots, row_base, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }
@@ -528,7 +541,7 @@ lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_
   auto kern = fold_first6_mma<V_RECORDS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
   kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(unused, unused, static_cast<const uint4 *>(a_dev), out, out_hi, n,
-                                           tile_begin, tile_end, entries, offs, shots, ctx->d_status);
+                                           tile_begin, tile_end, entries, offs, shots, 0, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }

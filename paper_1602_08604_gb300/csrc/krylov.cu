@@ -334,11 +334,11 @@ lre_status ritz_ends(lre_ctx *ctx, const KryBuffers &B, const double *alpha, con
   const double tol = 4.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN);
   const int m = CB + CT;
   {
-    Launch L(ctx, "kry_bisect", s, 2);
+    Launch L(ctx, "kry_bisect", s, 2);  // one warp per Ritz value, two per CTA
     if (CB > 0)
-      tri_bisect_kernel<<<(CB + 31) / 32, 32, 0, s>>>(alpha, B.b2, J, hst[0] - pad, hst[1] + pad, tol, pivmin, B.Wr,
-                                                       0, CB);
-    tri_bisect_kernel<<<(CT + 31) / 32, 32, 0, s>>>(alpha, B.b2, J, hst[0] - pad, hst[1] + pad, tol, pivmin,
+      tri_multisect_kernel<<<(CB + 1) / 2, 64, 0, s>>>(alpha, B.b2, J, hst[0] - pad, hst[1] + pad, tol, pivmin,
+                                                       B.Wr, 0, CB);
+    tri_multisect_kernel<<<(CT + 1) / 2, 64, 0, s>>>(alpha, B.b2, J, hst[0] - pad, hst[1] + pad, tol, pivmin,
                                                      B.Wr + CB, J - CT, CT);
   }
   int hk = 0;

@@ -49,7 +49,7 @@ struct lre_ctx {
   // pipeline fused with the second pass through L2 (correct, but slower on
   // GB300 so far: its second-pass jobs are L2-latency bound)
   int first_variant = 1;
-  int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores where the input allows
+  int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores for int16 counts, 2 also int32
   void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
   int mma_biased = 0;         // tensor-core operand: 0 raw counts as fp16 bits, 1 fp16(1024 + c)
   int project_mode = 1;       // step (iii): 1 eigenvalue-first where it applies, 0 full eigendecomposition
@@ -68,6 +68,13 @@ struct lre_ctx {
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
   cudaEvent_t ev_theta = nullptr;         // theta final: its copy-back may start
+  // streamed estimate (lre_stream_*): the instance, and the bases whose first
+  // fold pass is done (a prefix of whole tile rows)
+  int stream_active = 0;
+  int stream_n = 0;
+  lre_count_kind stream_kind = LRE_COUNTS_I16;
+  int64_t stream_shots = 0, stream_rows_done = 0;
+  void *stream_ws = nullptr;  // the workspace the streamed state lives in
 };
 
 namespace lre {
@@ -118,6 +125,9 @@ struct FoldArgs {
   // over tile rows ah_begin..ah_end) instead of dense counts
   const uint16_t *rec_entries = nullptr;
   const int32_t *rec_offs = nullptr;
+  // stage 1 only: `counts` holds rows [row_base, row_base + rows_in) of the
+  // count matrix (rows_in = 0: all 3^n rows from row 0)
+  int64_t row_base = 0, rows_in = 0;
 };
 size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound,
                             int variant = 2);
@@ -160,6 +170,8 @@ lre_status project_run(lre_ctx *ctx, const lre_c64 *rho_in, int n, lre_c64 *rho_
 constexpr int TRI_THREADS = 256;
 __global__ void tri_bisect_kernel(const double *a, const double *b2, int64_t n, double lo0, double hi0, double tol,
                                   double pivmin, double *W, int64_t j0, int64_t cnt);
+__global__ void tri_multisect_kernel(const double *a, const double *b2, int64_t n, double lo0, double hi0,
+                                     double tol, double pivmin, double *W, int64_t j0, int64_t cnt);
 // Gershgorin bounds of T (stats[0], stats[1]), the largest squared
 // off-diagonal (stats[2]) and the squares b2 (one CTA of 256 threads).
 __global__ void tri_prepare(const double *a, const double *b, int64_t n, double *b2, double *stats);
@@ -195,7 +207,9 @@ lre_status estimate_host_run(lre_ctx *ctx, const void *host_in, int host_kind, i
 
 // ---- tensor-core first pass (fold_mma.cu) ----------------------------------------
 size_t mma_operand_bytes();
-uint32_t mma_box_rows(int which);    // TMA box rows: 0 the 216-row box, 1 the 81-row tail
+// TMA box rows of the count maps: which 0 the main box (216 rows; SPLIT 108),
+// 1 the tail (81 rows)
+uint32_t mma_box_rows(int which, int variant);
 // largest count the operand encoding keeps exact: variant 0 raw int16 (2047),
 // 1 biased int16 (1023), 3 int32 in two planes (16383)
 int64_t mma_max_count(int variant);
@@ -208,7 +222,12 @@ lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_
                                   int64_t tile_end, cudaStream_t s);
 lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail, const void *a_dev,
                           int32_t *out, int8_t *out_hi, int n, int variant, int64_t shots, int64_t tile_begin,
-                          int64_t tile_end, cudaStream_t s);
+                          int64_t tile_end, int64_t row_base, cudaStream_t s);
+// Streamed first pass (lre_stream_*): the layout of the first pass's output
+// for these arguments -- split planes or int32, elements in all -- and
+// whether the arguments can be streamed at all (a six-qubit first pass that
+// takes tile ranges).
+bool fold_stage1_layout(lre_ctx *ctx, const FoldArgs &a, bool *planes, int64_t *elems);
 
 // ---- batched instances (one persistent launch) ---------------------------------
 lre_status batch_run(lre_ctx *ctx, const lre_instance *inst, int count, cudaStream_t s);

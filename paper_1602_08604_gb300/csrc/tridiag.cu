@@ -55,6 +55,38 @@ __global__ void tri_bisect_kernel(const double *a, const double *b2, int64_t n, 
   }
 }
 
+// The same eigenvalues by multisection, one warp per eigenvalue: each round
+// the 32 lanes split the bracket into 32 parts and evaluate the Sturm count at
+// the 31 inner points, so the bracket shrinks 32-fold per round (about 12
+// rounds to 4 eps ||T||) instead of 2-fold; for the few extreme eigenvalues a
+// Krylov check needs, which bisection would run on a handful of threads.
+// Warps beyond j0 + cnt idle; blockDim a multiple of 32.
+__global__ void tri_multisect_kernel(const double *a, const double *b2, int64_t n, double lo0, double hi0, double tol,
+                                     double pivmin, double *W, int64_t j0, int64_t cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t jj = wid; jj < cnt; jj += nw) {
+    const int64_t j = j0 + jj;
+    double lo = lo0, hi = hi0;  // invariant: count(lo) <= j < count(hi)
+    for (int it = 0; it < 40; ++it) {
+      if (hi - lo <= tol) break;
+      const double step = (hi - lo) / 32.0;
+      const double x = lo + step * (double)(lane + 1);  // lane 31: x = hi (not evaluated)
+      const bool below = lane < 31 && x > lo && x < hi && sturm_count(a, b2, n, x, pivmin) <= j;
+      // the points where count <= j form a prefix: the new lo is the last of them
+      const unsigned m = __ballot_sync(0xffffffffu, below);
+      const int k = m ? 31 - __clz(m) : -1;  // last lane with count(x) <= j
+      const double nlo = k >= 0 ? lo + step * (double)(k + 1) : lo;
+      const double nhi = k + 1 <= 30 ? lo + step * (double)(k + 2) : hi;
+      if (!(nhi < hi || nlo > lo)) break;  // no progress (rounding): the bracket is as tight as it gets
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) W[jj] = 0.5 * (lo + hi);
+  }
+}
+
 namespace {
 
 __device__ __forceinline__ double start_entry(int64_t i, int64_t j) {

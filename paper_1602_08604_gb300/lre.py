@@ -26,6 +26,7 @@ LRE_SHOTS_U16 = 2
 
 LRE_FOLD_FWHT = 0
 LRE_FOLD_TENSOR = 1
+LRE_FOLD_TENSOR_SPLIT = 2
 
 LRE_HOST_COUNTS_I32 = 0
 LRE_HOST_COUNTS_I16 = 1
@@ -51,6 +52,12 @@ SIGNATURES = [
     ("lre_estimate", _i, [_p, _p, _i, _p, _i64, _i, _p, _p, _p]),
     ("lre_slab_sums", _i, [_p, _p, _i, _i, _i64, _p, _p, _p]),
     ("lre_weight", _i, [_p, _p, _i, _i64, _i64, _i64, _p, _p]),
+    ("lre_estimate_ic4", _i, [_p, _p, _i, _i64, _i, _p, _p, _p]),
+    ("lre_stream_begin", _i, [_p, _i, _i, _i64]),
+    ("lre_stream_chunk", _i, [_p, _p, _i64, _i64, _p]),
+    ("lre_stream_end", _i, [_p, _p, _p, _p]),
+    ("lre_stream_checkpoint", _i, [_p, _p, _sz, ctypes.POINTER(_sz), _p]),
+    ("lre_stream_resume", _i, [_p, _p, _sz, _p]),
     ("lre_assemble", _i, [_p, _p, _i, _p, _p]),
     ("lre_assemble_noalloc", _i, [_p, _i, _p, _p]),
     ("lre_project", _i, [_p, _p, _i, _p, _p, _p, _p]),
@@ -180,6 +187,38 @@ def lre_weight(ctx, S, n, first, shots, theta, stream=None):
                              _stream(stream)), ctx)
 
 
+def lre_estimate_ic4(ctx, counts, shots, n, theta, rho=None, stream=None):
+    """The 4^n-operator estimate (|0>, |1>, |+>, |+i> per qubit) from Pauli counts."""
+    _check(load().lre_estimate_ic4(ctx, _ptr(counts), _kind(counts), int(shots), int(n), _ptr(theta), _ptr(rho),
+                                   _stream(stream)), ctx)
+
+
+def lre_stream_begin(ctx, n, kind, shots):
+    _check(load().lre_stream_begin(ctx, int(n), int(kind), int(shots)), ctx)
+
+
+def lre_stream_chunk(ctx, counts, first_basis, stream=None):
+    """counts: device [num_bases][2^n] tensor of bases first_basis..."""
+    _check(load().lre_stream_chunk(ctx, _ptr(counts), int(first_basis), int(counts.shape[0]), _stream(stream)), ctx)
+
+
+def lre_stream_end(ctx, theta, rho=None, stream=None):
+    _check(load().lre_stream_end(ctx, _ptr(theta), _ptr(rho), _stream(stream)), ctx)
+
+
+def lre_stream_checkpoint(ctx, stream=None):
+    """The streamed state as bytes (host memory)."""
+    need = ctypes.c_size_t()
+    _check(load().lre_stream_checkpoint(ctx, None, 0, ctypes.byref(need), _stream(stream)), ctx)
+    buf = ctypes.create_string_buffer(need.value)
+    _check(load().lre_stream_checkpoint(ctx, buf, need.value, ctypes.byref(need), _stream(stream)), ctx)
+    return buf.raw
+
+
+def lre_stream_resume(ctx, state, stream=None):
+    _check(load().lre_stream_resume(ctx, state, len(state), _stream(stream)), ctx)
+
+
 def lre_assemble(ctx, theta, n, rho, stream=None):
     _check(load().lre_assemble(ctx, _ptr(theta), int(n), _ptr(rho), _stream(stream)), ctx)
 
@@ -237,7 +276,8 @@ def lre_batch_schedule(ctx):
 
 
 def lre_set_fold_path(ctx, path):
-    """LRE_FOLD_TENSOR (default; tcgen05 first pass where it applies) or LRE_FOLD_FWHT."""
+    """LRE_FOLD_TENSOR (default; tcgen05 first pass for int16 counts), LRE_FOLD_TENSOR_SPLIT (also int32
+    counts, as two fp16 planes) or LRE_FOLD_FWHT."""
     _check(load().lre_set_fold_path(ctx, int(path)), ctx)
 
 

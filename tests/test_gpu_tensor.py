@@ -35,7 +35,7 @@ def _sums_by_path(torch, c, n, bound, biased=0):
         lre, ctx = ctx_and_lre()
         try:
             _set_variant(lre, ctx, biased)
-            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if tensor else lre.LRE_FOLD_FWHT)
+            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR_SPLIT if tensor else lre.LRE_FOLD_FWHT)
             S = torch.full((4 ** n,), -1, dtype=torch.int64, device="cuda")
             lre.lre_profile(ctx, True)
             lre.lre_parity_sums(ctx, c, n, S, row_total_bound=bound)

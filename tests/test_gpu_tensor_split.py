@@ -54,7 +54,7 @@ def test_split_theta_matches_oracle_at_largest_counts(shots):
     raw = _skewed_counts(n, shots, 17 + shots, np.int32)
     lre, ctx = ctx_and_lre()
     try:
-        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR_SPLIT)
         lre.lre_profile(ctx, True)
         theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
         rho = torch.empty((2 ** n, 2 ** n), dtype=torch.complex64, device="cuda")
@@ -106,7 +106,7 @@ def _bad_estimate(torch, raw, shots, n, variant=0):
     lre, ctx = ctx_and_lre()
     try:
         _set_variant(lre, ctx, variant)
-        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR_SPLIT)
         theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
         lre.lre_estimate(ctx, torch.from_numpy(raw).cuda(), shots, n, theta)
         with pytest.raises(lre.LreError) as e:
@@ -173,7 +173,7 @@ def test_rows_off_their_shots_within_range_match_oracle(dtype, shots):
     for path in ("tensor", "fwht"):
         lre, ctx = ctx_and_lre()
         try:
-            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if path == "tensor" else lre.LRE_FOLD_FWHT)
+            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR_SPLIT if path == "tensor" else lre.LRE_FOLD_FWHT)
             theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
             lre.lre_estimate(ctx, torch.from_numpy(raw).cuda(), shots, n, theta)
             lre.lre_sync(ctx)
