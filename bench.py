@@ -315,7 +315,7 @@ def run_e2e(args, wl, lre, torch, device, theta_dev):
 
 
 FIRST_PASS_KERNELS = ("fold_first6", "fold_first6_mma", "fold_first6_mma_split", "fold_first9_fused",
-                      "fold_first6_mma_records")
+                      "fold_first6_mma_records", "fold_first9_mma")
 
 
 def timed_steps(lre, ctx, torch, stream, step, steps, warmup):
@@ -374,12 +374,33 @@ def step_alg_bytes(wl):
     return 3 ** n * (2 ** n) * (2 if wl["kind"] == "i16" else 4) + 8 * 4 ** n * 2 + 8 * 4 ** n
 
 
-def arm_record(lre, torch, device, stream, counts, wl, workload, path, steps, warmup, theta_ref=None):
+def set_first_variant(lre, ctx, variant, consumers=0, discard=0):
+    """Test hooks: the first-pass variant (2: fused with the second pass), the
+    CTAs the fused tensor-core pass gives the second pass (0: default) and
+    whether that pass drops the ring lines it has read from L2."""
+    import ctypes
+    f = lre.load().lre_debug_set_first_pass
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_int
+    if f(ctx, int(variant)) != 0:
+        raise RuntimeError("first-pass variant rejected")
+    g = lre.load().lre_debug_set_fused_consumers
+    g.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    g.restype = ctypes.c_int
+    if g(ctx, int(consumers), int(discard)) != 0:
+        raise RuntimeError("fused-pass consumer count rejected")
+
+
+def arm_record(lre, torch, device, stream, counts, wl, workload, path, steps, warmup, theta_ref=None,
+               first_variant=None, consumers=0, discard=0):
     """One timed arm of lre_estimate on resident counts with the first fold
-    pass on the tensor cores or on the ALUs (FWHT), in a context of its own."""
+    pass on the tensor cores or on the ALUs (FWHT), in a context of its own;
+    first_variant 2: the first pass fused with the second through L2."""
     n = wl["n"]
     ctx = lre.lre_create(device.index)
     try:
+        if first_variant is not None:
+            set_first_variant(lre, ctx, first_variant, consumers, discard)
         lre.lre_set_fold_path(ctx, {"tensor": lre.LRE_FOLD_TENSOR, "tensor_split": lre.LRE_FOLD_TENSOR_SPLIT,
                                     "fwht": lre.LRE_FOLD_FWHT}[path])
         theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
@@ -474,6 +495,8 @@ def run_ours(args, wl):
     ctx = lre.lre_create(local)
     lre.lre_set_fold_path(ctx, {"tensor": lre.LRE_FOLD_TENSOR, "tensor_split": lre.LRE_FOLD_TENSOR_SPLIT,
                                 "fwht": lre.LRE_FOLD_FWHT}[args.fold_path])
+    if args.fused_first:
+        set_first_variant(lre, ctx, 2, args.fused_consumers, args.fused_discard)
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -507,6 +530,13 @@ def run_ours(args, wl):
         compare[f"{args.workload}_{other}"], _ = arm_record(
             lre, torch, device, stream, counts, wl, args.workload, other, args.compare_steps, 2, theta_ref=theta)
         torch.cuda.empty_cache()
+        if args.fold_path == "tensor" and not args.fused_first:
+            # the first pass fused with the second through an L2 ring
+            compare[f"{args.workload}_fused_first_second"], _ = arm_record(
+                lre, torch, device, stream, counts, wl, args.workload, "tensor", args.compare_steps, 2,
+                theta_ref=theta, first_variant=2, consumers=args.fused_consumers,
+                discard=args.fused_discard)
+            torch.cuda.empty_cache()
     projection = None
     if args.project and rank == 0:
         # step (iii), timed once on its own on the rho of the last step: the
@@ -610,7 +640,7 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "shots_per_basis": wl["shots"],
                        "counts_dtype": wl["kind"], "step": "lre_estimate: counts -> theta (FP64) -> rho (c64)",
-                       "fold_path": args.fold_path,
+                       "fold_path": args.fold_path, "fused_first_second": bool(args.fused_first),
                        "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": "independent instance per GPU" if world > 1 else "1 GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
@@ -857,6 +887,12 @@ def main():
     ap.add_argument("--fold-path", default="tensor", choices=["fwht", "tensor", "tensor_split"],
                     help="first fold pass on the tensor cores (the library default: int16 counts), also for "
                          "int32 counts as two fp16 planes (tensor_split), or on the ALUs (FWHT)")
+    ap.add_argument("--fused-first", action="store_true",
+                    help="the first fold pass fused with the second through an L2 ring (n >= 10)")
+    ap.add_argument("--fused-consumers", type=int, default=0,
+                    help="fused tensor-core pass: CTAs on the second pass (0: the library's default)")
+    ap.add_argument("--fused-discard", type=int, default=0, choices=(0, 1),
+                    help="fused tensor-core pass: drop the ring lines the second pass has read from L2")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the comparison arms (the other first-pass path on the same counts; for the "
                          "n=14 workload also the n=12 int32 workload on both paths and the batched launch)")

@@ -30,11 +30,16 @@ lre_status ensure_workspace(lre_ctx *ctx, size_t bytes) {
     ctx->ws_bytes = 0;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(workspace)");
   }
-  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  const size_t guard = ctx->canaries ? kCanaryBytes : 0;
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes + guard);
   if (e != cudaSuccess) {
     ctx->ws = nullptr;
     cudaGetLastError();
     return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+  }
+  if (guard) {  // the pattern every kernel must leave alone
+    e = cudaMemset(static_cast<char *>(ctx->ws) + bytes, kCanaryByte, guard);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace guard");
   }
   ctx->ws_bytes = bytes;
   return LRE_OK;
@@ -414,6 +419,27 @@ extern "C" lre_status lre_debug_set_first_pass(lre_ctx *ctx, int variant) {
   return LRE_OK;
 }
 
+// Test hook (not part of include/lre.h): CTAs that run the second pass in
+// the fused tensor-core first pass (0: the default, a sixth of the SMs), and
+// whether its second pass drops the ring lines it has read from L2 (1) or
+// leaves them to be overwritten (0, the default).
+extern "C" lre_status lre_debug_set_fused_consumers(lre_ctx *ctx, int ctas, int discard) {
+  if (!ctx || ctas < 0 || (ctas > 0 && ctas >= ctx->num_sms) || discard < 0 || discard > 1)
+    return LRE_ERR_INVALID_ARG;
+  ctx->fused_consumers = ctas;
+  ctx->fused_discard = discard;
+  return LRE_OK;
+}
+
+// Test hook (not part of include/lre.h): CTAs of the tensor-core first pass
+// (0: one per SM, the default; fewer leave SMs idle, to measure how its rate
+// grows with the SMs that run it).
+extern "C" lre_status lre_debug_set_first_grid(lre_ctx *ctx, int ctas) {
+  if (!ctx || ctas < 0 || ctas > ctx->num_sms) return LRE_ERR_INVALID_ARG;
+  ctx->first_grid = ctas;
+  return LRE_OK;
+}
+
 // Test hook (not part of include/lre.h): step (iii) through the default
 // choice (1: the Krylov path from d = 2048 on when eig_mu is not asked for,
 // else the eigenvalue-first path for d >= 64), always the eigenvalue-first
@@ -506,5 +532,44 @@ extern "C" lre_status lre_set_fold_path(lre_ctx *ctx, int path) {
   if (!ctx || (path != LRE_FOLD_FWHT && path != LRE_FOLD_TENSOR && path != LRE_FOLD_TENSOR_SPLIT))
     return LRE_ERR_INVALID_ARG;
   ctx->fold_path = path;
+  return LRE_OK;
+}
+
+// Test hook (not part of include/lre.h): workspace canaries.  on = 1 frees
+// the workspace and makes every later allocation carry a 64 KiB guard of a
+// fixed byte pattern after its usable end; lre_debug_check_canaries
+// synchronises the device and reports in *intact whether the guard is still
+// whole (1) or some call wrote past the workspace (0) -- a substitute for a
+// memory checker, on a pool where none runs.
+extern "C" lre_status lre_debug_set_canaries(lre_ctx *ctx, int on) {
+  if (!ctx || on < 0 || on > 1) return LRE_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LRE_ERR_CUDA;
+  if (ctx->ws) {
+    cudaError_t e = cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    for (auto &en : ctx->batch_cache) cudaFree(en.table);  // plans point into the old workspace
+    ctx->batch_cache.clear();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(workspace)");
+  }
+  ctx->canaries = on;
+  return LRE_OK;
+}
+
+extern "C" lre_status lre_debug_check_canaries(lre_ctx *ctx, int *intact) {
+  if (!ctx || !intact) return LRE_ERR_INVALID_ARG;
+  *intact = 1;
+  if (!ctx->canaries || !ctx->ws) return LRE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LRE_ERR_CUDA;
+  std::string host(kCanaryBytes, '\0');
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&host[0], static_cast<char *>(ctx->ws) + ctx->ws_bytes, kCanaryBytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace guard read");
+  for (size_t i = 0; i < kCanaryBytes; ++i)
+    if ((unsigned char)host[i] != kCanaryByte) {
+      *intact = 0;
+      break;
+    }
   return LRE_OK;
 }

@@ -660,11 +660,19 @@ bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, const void *b
   return r == CUDA_SUCCESS;
 }
 
-constexpr size_t FUSE_SCRATCH_BYTES = (size_t)FUSE_RING * 216 * 4096 * 4;
+// the ring and counters of whichever fused pass runs (ALU or tensor-core)
+size_t fuse_scratch_bytes() {
+  const size_t alu = (size_t)FUSE_RING * 216 * 4096 * 4, mma = mma_fused9_scratch_bytes();
+  return round_up(alu > mma ? alu : mma);
+}
+size_t fuse_counter_bytes() {
+  const size_t alu = sizeof(FuseState), mma = mma_fused9_counter_bytes();
+  return round_up(alu > mma ? alu : mma);
+}
 
 size_t fuse_bytes(const std::vector<PassPlan> &plan) {
   for (const auto &pp : plan)
-    if (pp.fused9) return round_up(FUSE_SCRATCH_BYTES) + round_up(sizeof(FuseState));
+    if (pp.fused9) return fuse_scratch_bytes() + fuse_counter_bytes();
   return 0;
 }
 
@@ -690,10 +698,10 @@ namespace {
 // Operand variant of the tensor-core first pass for this pass (0 raw int16,
 // 1 biased int16, 3 int32 in two planes), or -1 when the ALU pass runs.
 int tensor_variant(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
-  if (!pp.first6 || pp.fused9 || ctx->fold_path < 1 || !ctx->mma_operand || a.shots != nullptr ||
-      a.shots_uniform <= 0)
+  if (!pp.first6 || ctx->fold_path < 1 || !ctx->mma_operand || a.shots != nullptr || a.shots_uniform <= 0)
     return -1;
   const int v = pp.in_t == T_I16 ? ctx->mma_biased : (pp.in_t == T_I32 && ctx->fold_path == 2 ? 3 : -1);
+  if (pp.fused9 && v != 0) return -1;  // the fused first + second pass exists for the raw encoding
   return v >= 0 && a.shots_uniform <= mma_max_count(v) ? v : -1;
 }
 
@@ -705,7 +713,7 @@ bool tensor_first_pass(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
 // must stay below 2^23) as split planes (3 bytes instead of 4) when the next
 // pass is a TMA-staged store pass that reads them back.
 bool use_planes(lre_ctx *ctx, const std::vector<PassPlan> &plan, const FoldArgs &a) {
-  return !plan.empty() && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
+  return !plan.empty() && !plan[0].fused9 && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
          a.shots_uniform * 729 < (1ll << 23) && plan[1].mode == M_STORE && plan[1].in_t == T_I32 &&
          ctx->generic_tma && plan[1].C % 32 == 0;
 }
@@ -752,7 +760,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
   double *wgt = reinterpret_cast<double *>(p + round_up(bA) + round_up(bB));
   int32_t *fuse_scratch = reinterpret_cast<int32_t *>(p + round_up(bA) + round_up(bB) + wbytes);
   FuseState *fuse_state = reinterpret_cast<FuseState *>(reinterpret_cast<char *>(fuse_scratch) +
-                                                         round_up(FUSE_SCRATCH_BYTES));
+                                                         fuse_scratch_bytes());
   const size_t need = round_up(bA) + round_up(bB) + wbytes + fuse_bytes(plan);
   if (need > ws_bytes) return LRE_ERR_OOM;
   const int64_t B = ipow(3, a.n);
@@ -792,6 +800,17 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       int8_t *hi = planes ? static_cast<int8_t *>(out) + elems * 2 : nullptr;
       lre_status st = mma_first_pass_records(ctx, ctx->mma_operand, a.rec_entries, a.rec_offs, a.shots_uniform,
                                              static_cast<int32_t *>(out), hi, pp.r, tile_begin, tile_end, s);
+      if (st != LRE_OK) return st;
+    } else if (tensor && pp.fused9) {
+      const int64_t rows = ipow(3, pp.r);
+      if (!make_count_map(&tmap, in, LRE_COUNTS_I16, pp.r, rows, mma_box_rows(0, 0)) ||
+          !make_count_map(&tmap_tail, in, LRE_COUNTS_I16, pp.r, rows, mma_box_rows(1, 0))) {
+        ctx->last_error = "tensor map of the counts rejected";
+        return LRE_ERR_CUDA;
+      }
+      lre_status st = mma_first_pass_fused9(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out),
+                                            fuse_scratch, reinterpret_cast<unsigned *>(fuse_state), pp.r,
+                                            a.shots_uniform, ctx->fused_consumers, ctx->fused_discard != 0, s);
       if (st != LRE_OK) return st;
     } else if (tensor) {
       const lre_count_kind mk = pp.in_t == T_I16 ? LRE_COUNTS_I16 : LRE_COUNTS_I32;

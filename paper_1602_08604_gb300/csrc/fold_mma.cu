@@ -79,7 +79,29 @@ namespace {
 
 using namespace passes;
 
-enum : int { V_RAW = 0, V_BIASED = 1, V_RECORDS = 2, V_SPLIT = 3 };
+enum : int { V_RAW = 0, V_BIASED = 1, V_RECORDS = 2, V_SPLIT = 3, V_RAW9 = 4 };
+
+// V_RAW9: the raw pass fused with the second fold pass (three more qubits)
+// through L2, in one cooperative launch whose CTAs take one of two roles.
+// CTAs 0..np1-1 run the raw pass over the tiles in group-major order (a group
+// = the 27 x 8 tiles one second-pass column reads: the low ternary digits of
+// ah and the low bits of oh), counts streamed with an evict-first hint; their
+// level-B warps write a tile's 4096 int32 partials into slot G mod F9_RING of
+// a scratch ring (3.5 MB per group, small enough to stay in L2) and count the
+// tile in tiles_done[slot].  The other CTAs run the second pass: each of their
+// eight warps takes jobs (a group and 32 columns) cw, cw + W, ... in order,
+// waits for the group's tiles, has TMA bring the job's 216 rows x 32 columns
+// from the ring into its own shared-memory buffer (27 KB; eight loads in
+// flight per SM), contracts al2, ol2, stores the 64 outputs, drops the
+// consumed 128-byte lines from L2 without write-back and counts the job in
+// jobs_done[slot], which the level-B warps wait for before reusing the slot.
+// Every wait points at an earlier group and every warp takes its jobs in
+// increasing order, so the smallest unfinished tile can always proceed; the
+// cooperative launch makes every CTA resident.
+constexpr int F9_RING = 16;
+constexpr int F9_JOBS = 4096 / 32;             // second-pass jobs per group
+constexpr int F9_WARPS = 8;                    // second-pass warps per CTA
+constexpr int F9_BOX = 216 * 32 * 4;           // one job's rows: 216 x 32 int32
 
 constexpr int MMA_THREADS = 256;
 constexpr int MMA_R = 3;                       // ring slots of one chunk each
@@ -103,7 +125,7 @@ struct MmaCfg {
   static constexpr int CPT = V == V_SPLIT ? SPLIT_CHUNKS : 2;       // chunks per tile
   static constexpr int R = MMA_R;                                     // ring slots
   static constexpr int SLOT = SLOT_BYTES;
-  static constexpr int THREADS = V == V_SPLIT ? 320 : 256;           // + warps 8, 9 convert
+  static constexpr int THREADS = V == V_SPLIT ? 320 : 256;  // + converters
   static constexpr int CONV_WARPS = V == V_SPLIT ? 4 : 2;            // arrivals on conv: 32 each
 };
 constexpr int A_BYTES = 16 * 28 * 128;         // 128 x 224 fp16, core-matrix layout
@@ -115,6 +137,7 @@ constexpr uint32_t TMEM_COLS = 512;            // two tile accumulators
 constexpr uint32_t TILE_COLS = 256;
 constexpr uint32_t BOX_BIG = 216, BOX_TAIL = 81;  // TMA boxes: 8 and 3 alB groups
 static_assert(MMA_SMEM <= 232448, "shared memory of one CTA");
+static_assert(F9_WARPS * (F9_BOX + 8) + 1024 <= MMA_SMEM, "second-pass buffers and barriers fit");
 static_assert(2 * BOX_BIG <= CHUNK_ROWS && BOX_BIG + BOX_TAIL <= CHUNK_ROWS, "chunk fits its slot");
 // the N = 96 chain reads alB = 27 (rows 729..755 of the tile): still inside the slot
 static_assert(12 * 27 <= CHUNK_ROWS, "padded alB group stays in the slot");
@@ -138,10 +161,14 @@ __device__ __forceinline__ int32_t d_to_int(uint32_t bits, float scale, int32_t 
 template <int V>
 __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     fold_first6_mma(const __grid_constant__ CUtensorMap map_big, const __grid_constant__ CUtensorMap map_tail,
-                    const uint4 *__restrict__ gA, int32_t *__restrict__ out, int8_t *__restrict__ out_hi, int n,
+                    const __grid_constant__ CUtensorMap map_s, int np1, int f9_opts, const uint4 *__restrict__ gA,
+                    int32_t *__restrict__ out, int8_t *__restrict__ out_hi, int n,
                     int64_t tile_begin, int64_t tile_end, const uint16_t *__restrict__ entries,
-                    const int32_t *__restrict__ offs, int64_t shots, int64_t row_base, int *status) {
+                    const int32_t *__restrict__ offs, int64_t shots, int64_t row_base, int32_t *__restrict__ scratch,
+                    unsigned *__restrict__ f9, int *status) {
   constexpr bool BIASED = V == V_BIASED, RECORDS = V == V_RECORDS, SPLIT = V == V_SPLIT;
+  constexpr bool RAWLIKE = V == V_RAW || V == V_RAW9, F9 = V == V_RAW9;
+  // F9 counters: f9[0] the next job, f9[1 + s] tiles done, f9[1 + F9_RING + s] jobs done (slot s)
   constexpr int CPT = MmaCfg<V>::CPT;
   constexpr int MR = MmaCfg<V>::R;          // ring slots
   constexpr int SLOT = MmaCfg<V>::SLOT;     // bytes per slot
@@ -158,39 +185,130 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_oh = (1ll << n) >> 6;
+  // F9: CTAs np1.. run the second pass; the first np1 share the tiles
+  const bool consumer = F9 && (int)blockIdx.x >= np1;
+  const int nP = F9 ? np1 : (int)gridDim.x;
 
-  for (int i = threadIdx.x; i < A_BYTES / 16; i += MmaCfg<V>::THREADS) reinterpret_cast<uint4 *>(Am)[i] = gA[i];
-  if (threadIdx.x == 0) {
+  if (!consumer)
+    for (int i = threadIdx.x; i < A_BYTES / 16; i += MmaCfg<V>::THREADS) reinterpret_cast<uint4 *>(Am)[i] = gA[i];
+  if (threadIdx.x == 0) *abort_flag = 0;
+  if (threadIdx.x == 0 && !consumer) {
     for (int i = 0; i < MR; ++i) {
       sm103::mbar_init(&full[i], 1);
       sm103::mbar_init(&conv[i], 32 * MmaCfg<V>::CONV_WARPS);
       // RAW: released by the MMAs' commit and by the two range-check warps,
       // which read the slot while the MMAs run
-      sm103::mbar_init(&empty[i], V == V_RAW ? 3 : 1);
+      sm103::mbar_init(&empty[i], RAWLIKE ? 3 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       sm103::mbar_init(&tile_done[b], 1);
       sm103::mbar_init(&tile_free[b], 64);
     }
-    *abort_flag = 0;
     sm103::fence_barrier_init();
   }
   sm103::fence_proxy_async_smem();  // A is read by the tensor cores
-  if (warp == 1) sm103::tmem_alloc(tmem_slot, TMEM_COLS);
+  if (warp == 1 && !consumer) sm103::tmem_alloc(tmem_slot, TMEM_COLS);
   sm103::tc_fence_before();
   __syncthreads();
   sm103::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = consumer ? 0u : *tmem_slot;
   auto give_up = [&]() {
     *abort_flag = 1;
     latch(status, LRE_ERR_TIMEOUT);
   };
   const int64_t tiles = tile_end - tile_begin;
-  const int64_t my_tiles = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t my_tiles = (!consumer && tiles > blockIdx.x) ? (tiles - blockIdx.x + nP - 1) / nP : 0;
   const int64_t total = my_tiles * CPT;  // chunks of this CTA
   const bool conv_warp = SPLIT ? (warp == 2 || warp == 3 || warp == 8 || warp == 9) : (warp == 2 || warp == 3);
 
-  if (RECORDS && (warp == 0 || warp == 2 || warp == 3)) {
+  if (consumer) {
+    // second pass (qubits 7..9): warp cw takes jobs cw, cw + W, ...; a job is
+    // a group and 32 of its 4096 columns, output [G][64][4096] as the unfused
+    // second pass writes it.  The ring slot is released as soon as the job's
+    // copy has landed, and the next job's copy is in flight while this job's
+    // outputs are stored.
+    uint8_t *buf = smem + warp * F9_BOX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + F9_WARPS * F9_BOX) + warp;
+    if (lane == 0) {
+      sm103::mbar_init(bar, 1);
+      sm103::fence_barrier_init();
+    }
+    __syncwarp();
+    const int64_t total_jobs = tiles / 216 * F9_JOBS;
+    const int64_t W = (int64_t)(gridDim.x - np1) * F9_WARPS;
+    const bool discard = (f9_opts & 1) != 0;
+    // lane 0 waits for job j's group, then has TMA bring the job's rows into buf
+    auto fetch = [&](int64_t j) -> bool {
+      int ok = 1;
+      if (lane == 0) {
+        const int64_t G = j / F9_JOBS;
+        const int slot = (int)(G % F9_RING);
+        ok = sm103::poll_geq(f9 + 1 + slot, (unsigned)(2 * 216 * (G / F9_RING + 1)), abort_flag);
+        if (ok) {
+          // the tiles' generic-proxy stores, acquired above, before the async-proxy
+          // read; this buffer's last generic reads before the copy overwrites it
+          sm103::fence_proxy_async_global();
+          sm103::fence_proxy_async_smem();
+          sm103::mbar_arrive_expect_tx(bar, F9_BOX);
+          sm103::tma_load_2d(buf, &map_s, (int)(j % F9_JOBS) * 32, slot * 216, bar);
+        }
+      }
+      return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
+    int64_t j = (int64_t)(blockIdx.x - np1) * F9_WARPS + warp;
+    bool inflight = false;
+    if (j < total_jobs) {
+      inflight = fetch(j);
+      if (!inflight) give_up();
+    }
+    uint32_t phase = 0;
+    while (inflight) {
+      inflight = false;
+      if (!sm103::mbar_wait(bar, phase, abort_flag)) {
+        give_up();
+        for (uint32_t it = 0; it < sm103::kSpinLimit; ++it)  // the copy in flight lands first
+          if (sm103::mbar_try_wait(bar, phase)) break;
+        break;
+      }
+      phase ^= 1u;
+      const int64_t G = j / F9_JOBS;
+      const int chunk = (int)(j % F9_JOBS);
+      const int slot = (int)(G % F9_RING);
+      if (discard) {
+        // the 216 consumed 128-byte lines are dead: drop them from L2 unwritten,
+        // ordered before the count that lets the slot be rewritten
+        const int32_t *line0 = scratch + (int64_t)slot * 216 * 4096 + chunk * 32;
+        for (int r = lane; r < 216; r += 32)
+          asm volatile("discard.global.L2 [%0], 128;" ::"l"(line0 + r * 4096) : "memory");
+        __threadfence();
+      }
+      __syncwarp();
+      if (lane == 0) atomicAdd(f9 + 1 + F9_RING + slot, 1u);  // the copy has landed: slot reusable
+      const int32_t *src = reinterpret_cast<const int32_t *>(buf) + lane;
+      int32_t acc[64];
+#pragma unroll
+      for (int p = 0; p < 64; ++p) acc[p] = 0;
+#pragma unroll
+      for (int al2 = 0; al2 < 27; ++al2) {  // unrolled: the Pauli digits index registers
+        int32_t v[8];
+#pragma unroll
+        for (int ol2 = 0; ol2 < 8; ++ol2) v[ol2] = src[(al2 * 8 + ol2) * 32];
+        wht<3>(v);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[block_pauli(al2, m, 3)] += v[m];
+      }
+      __syncwarp();  // buf fully read before the next copy overwrites it
+      const int64_t jn = j + W;
+      if (jn < total_jobs) {
+        inflight = fetch(jn);
+        if (!inflight) give_up();
+      }
+      int32_t *o = out + G * 64 * 4096 + chunk * 32 + lane;
+#pragma unroll
+      for (int p = 0; p < 64; ++p) __stcs(o + p * 4096, acc[p]);
+      j = jn;
+    }
+  } else if (RECORDS && (warp == 0 || warp == 2 || warp == 3)) {
     const int bw = warp == 0 ? 0 : warp - 1;  // builder of chunks g = bw (mod 3): always slot bw
     const int64_t tr0 = tile_begin / n_oh;
     const int64_t row_entries = 729 * shots;
@@ -202,7 +320,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     int32_t pe0 = 0, pe1 = -1;
     int pbase = 0;
     for (int64_t g = bw; g < total; g += MR) {
-      const int64_t tile = tile_begin + blockIdx.x + (g >> 1) * gridDim.x;
+      const int64_t tile = tile_begin + blockIdx.x + (g >> 1) * nP;
       const int c = (int)(g & 1);
       const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
       if (g >= MR && !sm103::mbar_wait(&empty[bw], (uint32_t)((g / MR - 1) & 1), abort_flag)) {
@@ -250,9 +368,18 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     if (lane == 0) {
       int64_t g = 0;
       for (; g < total && !*abort_flag; ++g) {
-        const int64_t tile = tile_begin + blockIdx.x + (g / CPT) * gridDim.x;
+        const int64_t tile = tile_begin + blockIdx.x + (g / CPT) * nP;
         const int c = (int)(g % CPT);
-        const int64_t ah = tile / n_oh, oh = tile - ah * n_oh;
+        int64_t ah, oh;
+        if constexpr (F9) {  // group-major: group G = (gah, goh), k = (al2, ol2)
+          const int64_t G = tile / 216, k = tile - G * 216, n_goh = n_oh >> 3;
+          const int64_t gah = G / n_goh, goh = G - gah * n_goh;
+          ah = gah * 27 + k / 8;
+          oh = goh * 8 + (k & 7);
+        } else {
+          ah = tile / n_oh;
+          oh = tile - ah * n_oh;
+        }
         const int slot = (int)(g % MR);
         if (g >= MR && !sm103::mbar_wait(&empty[slot], (uint32_t)((g / MR - 1) & 1), abort_flag)) {
           give_up();
@@ -267,11 +394,18 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         } else {
           const int y = (int)(ah * 729 + c * 432 - row_base);
           sm103::mbar_arrive_expect_tx(&full[slot], (BOX_BIG + (c ? BOX_TAIL : BOX_BIG)) * 128);
-          sm103::tma_load_2d(dst, &map_big, x, y, &full[slot]);
-          if (c == 0)
-            sm103::tma_load_2d(dst + BOX_BIG * 128, &map_big, x, y + (int)BOX_BIG, &full[slot]);
-          else
-            sm103::tma_load_2d(dst + BOX_BIG * 128, &map_tail, x, y + (int)BOX_BIG, &full[slot]);
+          if constexpr (F9) {  // counts are read once: keep the scratch ring in L2 instead
+            const uint64_t pol = sm103::l2_evict_first();
+            sm103::tma_load_2d_hint(dst, &map_big, x, y, &full[slot], pol);
+            sm103::tma_load_2d_hint(dst + BOX_BIG * 128, c == 0 ? &map_big : &map_tail, x, y + (int)BOX_BIG,
+                                    &full[slot], pol);
+          } else {
+            sm103::tma_load_2d(dst, &map_big, x, y, &full[slot]);
+            if (c == 0)
+              sm103::tma_load_2d(dst + BOX_BIG * 128, &map_big, x, y + (int)BOX_BIG, &full[slot]);
+            else
+              sm103::tma_load_2d(dst + BOX_BIG * 128, &map_tail, x, y + (int)BOX_BIG, &full[slot]);
+          }
         }
       }
       for (int64_t q = g > MR ? g - MR : 0; q < g; ++q)  // drain in-flight loads
@@ -291,7 +425,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         give_up();
         break;
       }
-      if (!sm103::mbar_wait((RECORDS || V == V_RAW) ? &full[slot] : &conv[slot], (uint32_t)((g / MR) & 1),
+      if (!sm103::mbar_wait((RECORDS || RAWLIKE) ? &full[slot] : &conv[slot], (uint32_t)((g / MR) & 1),
                             abort_flag)) {
         give_up();
         break;
@@ -386,7 +520,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
           }
         }
       }
-      if constexpr (V == V_RAW) {  // done reading: one arrival per warp on the slot's release
+      if constexpr (RAWLIKE) {  // done reading: one arrival per warp on the slot's release
         __syncwarp();
         if (lane == 0) sm103::mbar_arrive(&empty[slot]);
       } else {
@@ -406,6 +540,15 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     const int plA = (quarter & 1) * 32 + lane;
     const float scale = BIASED ? 1.f : 16777216.f;
     const int32_t sub = BIASED && plA == 0 ? BIAS : 0;
+    int pend = -1;  // F9: ring slot of this warp's last tile, written but not yet counted
+    // F9: make this warp's ring stores visible (TMA reads them back, through
+    // the async proxy) and count the tile; two warps per tile
+    auto publish = [&](int slot) {
+      sm103::fence_proxy_async_global();
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicAdd(f9 + 1 + slot, 1u);
+    };
     for (int64_t lt = pair; lt < my_tiles; lt += 2) {
       if (!sm103::mbar_wait(&tile_done[pair], (uint32_t)((lt >> 1) & 1), abort_flag)) {
         give_up();
@@ -416,18 +559,21 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
       int32_t acc[64];
 #pragma unroll
       for (int p = 0; p < 64; ++p) acc[p] = 0;
+      // columns 32 grp .. 32 grp + 31 hold alB = 4 grp .. 4 grp + 3; the load of
+      // the next 32 columns is in flight while these are contracted
+      uint32_t r[2][32];
+      sm103::tmem_ld32(ta, r[0]);
 #pragma unroll
-      for (int grp = 0; grp < 7; ++grp) {  // columns 32 grp .. 32 grp + 31: alB = 4 grp .. 4 grp + 3
-        uint32_t r[32];
-        sm103::tmem_ld32(ta + grp * 32, r);
-        sm103::tmem_ld_wait();
+      for (int grp = 0; grp < 7; ++grp) {
+        sm103::tmem_ld_wait(r[grp & 1]);
+        if (grp < 6) sm103::tmem_ld32(ta + (grp + 1) * 32, r[(grp + 1) & 1]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int alB = grp * 4 + j;
           if (alB < 27) {
             int32_t v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = d_to_int(r[j * 8 + i], scale, sub);
+            for (int i = 0; i < 8; ++i) v[i] = d_to_int(r[grp & 1][j * 8 + i], scale, sub);
             wht<3>(v);
 #pragma unroll
             for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
@@ -436,8 +582,26 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
       }
       sm103::tc_fence_before();
       sm103::mbar_arrive(&tile_free[pair]);
-      const int64_t tile = tile_begin + blockIdx.x + lt * gridDim.x;
-      if (out_hi) {  // split planes: low 16 bits, then the (signed) bits above
+      const int64_t tile = tile_begin + blockIdx.x + lt * nP;
+      if constexpr (F9) {
+        // the previous tile's stores have had this tile's work to complete:
+        // count it now, so that its fence does not wait on them
+        if (pend >= 0) publish(pend);
+        pend = -1;
+        // into the group's ring slot, once that slot's previous group has been
+        // read by all of its second-pass jobs
+        const int64_t G = tile / 216, k = tile - G * 216;
+        const int slot = (int)(G % F9_RING);
+        const unsigned need = (unsigned)(F9_JOBS * (G / F9_RING));
+        if (need && !sm103::poll_geq(f9 + 1 + F9_RING + slot, need, abort_flag)) {
+          give_up();
+          break;
+        }
+        int32_t *o = scratch + ((int64_t)slot * 216 + k) * 4096 + plA;
+#pragma unroll
+        for (int p = 0; p < 64; ++p) o[p * 64] = acc[p];  // stays in L2 for the second pass
+        pend = slot;
+      } else if (out_hi) {  // split planes: low 16 bits, then the (signed) bits above
         unsigned short *lo = reinterpret_cast<unsigned short *>(out) + tile * 4096 + plA;
         signed char *hi = reinterpret_cast<signed char *>(out_hi) + tile * 4096 + plA;
 #pragma unroll
@@ -451,10 +615,11 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
       }
     }
+    if (F9 && pend >= 0) publish(pend);
   }
   sm103::tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 1 && !consumer) {
     sm103::tc_fence_after();
     sm103::tmem_dealloc(tmem, TMEM_COLS);
   }
@@ -514,17 +679,72 @@ lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtens
   if (tiles <= 0) return LRE_OK;
   if (shots <= 0 || shots > mma_max_count(variant) || (variant != 0 && variant != 1 && variant != 3))
     return LRE_ERR_UNSUPPORTED;
-  const int grid = (int)(tiles < ctx->num_sms ? tiles : ctx->num_sms);
+  const int ctas = ctx->first_grid > 0 ? ctx->first_grid : ctx->num_sms;
+  const int grid = (int)(tiles < ctas ? tiles : ctas);
   Launch L(ctx, variant == 3 ? "fold_first6_mma_split" : "fold_first6_mma", s);
   auto kern = variant == 3 ? fold_first6_mma<V_SPLIT>
                            : (variant == 1 ? fold_first6_mma<V_BIASED> : fold_first6_mma<V_RAW>);
   const int threads = variant == 3 ? MmaCfg<V_SPLIT>::THREADS : MMA_THREADS;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
-  kern<<<grid, threads, MMA_SMEM, s>>>(map_big, map_tail, static_cast<const uint4 *>(a_dev), out, out_hi, n,
-                                       tile_begin, tile_end, nullptr, nullptr, shots, row_base, ctx->d_status);
+  kern<<<grid, threads, MMA_SMEM, s>>>(map_big, map_tail, map_tail, grid, 0, static_cast<const uint4 *>(a_dev), out,
+                                       out_hi, n, tile_begin, tile_end, nullptr, nullptr, shots, row_base, nullptr,
+                                       nullptr, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }
+
+// The raw pass fused with the second fold pass (V_RAW9) over all tiles of an
+// n-qubit int16 count matrix (n >= 10): out receives the second pass's
+// output [groups][64][4096] int32; scratch is the L2 ring (F9_RING x 216 x
+// 4096 int32) and f9 its 1 + 2 F9_RING counters, zeroed here.  consumers:
+// the CTAs that run the second pass (0: a sixth of the SMs); discard: drop
+// each consumed ring line from L2 without write-back (one fence per job).
+// One CTA per SM, launched cooperatively, since the two roles wait on each
+// other.
+lre_status mma_first_pass_fused9(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail,
+                                 const void *a_dev, int32_t *out, int32_t *scratch, unsigned *f9, int n,
+                                 int64_t shots, int consumers, bool discard, cudaStream_t s) {
+  const int64_t tiles = ipow(3, n - 6) << (n - 6);
+  if (n < 10 || shots <= 0 || shots > mma_max_count(0) || tiles % 216 != 0) return LRE_ERR_UNSUPPORTED;
+  const int grid = ctx->num_sms;
+  const int q = consumers > 0 ? consumers : grid / 6;
+  if (q < 1 || q >= grid) return LRE_ERR_INVALID_ARG;
+  CUtensorMap map_s;
+  const uint64_t dims[2] = {4096, (uint64_t)F9_RING * 216};
+  const uint64_t strides[1] = {4096 * 4};
+  const uint32_t box[2] = {32, 216};
+  if (!encode_tensor_map_i32(&map_s, scratch, 2, dims, strides, box)) {
+    ctx->last_error = "tensor map of the fused pass's ring rejected";
+    return LRE_ERR_CUDA;
+  }
+  cudaError_t e = cudaMemsetAsync(f9, 0, (1 + 2 * F9_RING) * sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fused pass counters");
+  Launch L(ctx, "fold_first9_mma", s);
+  auto kern = fold_first6_mma<V_RAW9>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(MmaCfg<V_RAW9>::THREADS);
+  cfg.dynamicSmemBytes = MMA_SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const uint4 *a4 = static_cast<const uint4 *>(a_dev);
+  int8_t *no_hi = nullptr;
+  const uint16_t *no_ent = nullptr;
+  const int32_t *no_offs = nullptr;
+  const int np1 = grid - q;
+  const int64_t t0 = 0, r0 = 0;
+  const int opts = discard ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, kern, map_big, map_tail, map_s, np1, opts, a4, out, no_hi, n, t0, tiles, no_ent,
+                         no_offs, shots, r0, scratch, f9, ctx->d_status);
+  return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "fused tensor-core pass launch");
+}
+size_t mma_fused9_scratch_bytes() { return (size_t)F9_RING * 216 * 4096 * 4; }
+size_t mma_fused9_counter_bytes() { return (1 + 2 * F9_RING) * sizeof(unsigned); }
 
 // The same pass over tiles [tile_begin, tile_end) whose counts come from shot
 // records grouped by tile (tile_bucket_run over the tile rows from
@@ -540,8 +760,9 @@ lre_status mma_first_pass_records(lre_ctx *ctx, const void *a_dev, const uint16_
   Launch L(ctx, "fold_first6_mma_records", s);
   auto kern = fold_first6_mma<V_RECORDS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
-  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(unused, unused, static_cast<const uint4 *>(a_dev), out, out_hi, n,
-                                           tile_begin, tile_end, entries, offs, shots, 0, ctx->d_status);
+  kern<<<grid, MMA_THREADS, MMA_SMEM, s>>>(unused, unused, unused, grid, 0, static_cast<const uint4 *>(a_dev), out,
+                                           out_hi, n, tile_begin, tile_end, entries, offs, shots, 0, nullptr,
+                                           nullptr, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "tensor-core first pass launch");
 }

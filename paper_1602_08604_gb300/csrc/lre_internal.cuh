@@ -45,10 +45,13 @@ struct lre_ctx {
   std::vector<lre_prof_entry> prof_pool;  // reused events
   size_t prof_used = 0;
   uint64_t launches = 0;                  // kernels of this library launched so far
-  // ALU first fold pass: 0 register kernel, 1 TMA pipeline (default), 2 TMA
-  // pipeline fused with the second pass through L2 (correct, but slower on
-  // GB300 so far: its second-pass jobs are L2-latency bound)
+  // first fold pass: 0 register kernel, 1 TMA pipeline (default), 2 fused
+  // with the second pass through L2 (the ALU pipeline, or the tensor-core
+  // pass where that runs)
   int first_variant = 1;
+  int fused_consumers = 0;    // tensor-core fused pass: CTAs on the second pass (0: a sixth of the SMs)
+  int fused_discard = 0;      // tensor-core fused pass: 1 = drop consumed ring lines from L2
+  int first_grid = 0;         // tensor-core first pass: CTAs (0: one per SM)
   int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores for int16 counts, 2 also int32
   void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
   int mma_biased = 0;         // tensor-core operand: 0 raw counts as fp16 bits, 1 fp16(1024 + c)
@@ -75,7 +78,10 @@ struct lre_ctx {
   lre_count_kind stream_kind = LRE_COUNTS_I16;
   int64_t stream_shots = 0, stream_rows_done = 0;
   void *stream_ws = nullptr;  // the workspace the streamed state lives in
+  int canaries = 0;           // test hook: a patterned guard after the workspace
 };
+constexpr size_t kCanaryBytes = 1 << 16;
+constexpr unsigned char kCanaryByte = 0xA5;
 
 namespace lre {
 
@@ -214,6 +220,12 @@ uint32_t mma_box_rows(int which, int variant);
 // 1 biased int16 (1023), 3 int32 in two planes (16383)
 int64_t mma_max_count(int variant);
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
+// the raw tensor-core pass fused with the second fold pass through an L2 ring
+lre_status mma_first_pass_fused9(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail,
+                                 const void *a_dev, int32_t *out, int32_t *scratch, unsigned *f9, int n,
+                                 int64_t shots, int consumers, bool discard, cudaStream_t s);
+size_t mma_fused9_scratch_bytes();
+size_t mma_fused9_counter_bytes();
 // records grouped by count tile (records.cu) and the first pass over them
 lre_status tile_bucket_run(lre_ctx *ctx, const uint16_t *records, int64_t tile_rows, int64_t shots, int n,
                            uint16_t *entries, int32_t *offs, cudaStream_t s);

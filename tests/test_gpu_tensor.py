@@ -138,3 +138,36 @@ def test_split_plane_theta_matches_oracle():
         lre.lre_destroy(ctx)
 
 
+@pytest.mark.parametrize("n,consumers,discard", [(10, 0, 0), (11, 0, 0), (12, 0, 0), (12, 1, 0), (12, 100, 1),
+                                                 (12, 0, 1)])
+def test_fused_first_and_second_pass_equals_unfused(n, consumers, discard):
+    """The tensor-core first pass fused with the second through an L2 ring
+    (test hook: first-pass variant 2; consumers: CTAs on the second pass, 0
+    the default; discard: consumed ring lines dropped from L2) gives the
+    unfused path's parity sums and theta bit for bit."""
+    torch = need_gpu()
+    c = _counts(torch, n, 1000, 60 + n)
+    out = []
+    for variant in (1, 2):
+        lre, ctx = ctx_and_lre()
+        try:
+            f = lre.load().lre_debug_set_first_pass
+            f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            f.restype = ctypes.c_int
+            assert f(ctx, variant) == 0
+            g = lre.load().lre_debug_set_fused_consumers
+            g.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+            g.restype = ctypes.c_int
+            assert g(ctx, consumers, discard) == 0
+            lre.lre_profile(ctx, True)
+            S = torch.full((4 ** n,), -1, dtype=torch.int64, device="cuda")
+            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=1000)
+            theta = torch.full((4 ** n,), float("nan"), dtype=torch.float64, device="cuda")
+            lre.lre_estimate(ctx, c, 1000, n, theta)
+            lre.lre_sync(ctx)
+            names = [k for k, _ in lre.lre_profile_records(ctx)]
+            assert ("fold_first9_mma" in names) == (variant == 2), names
+            out.append((S, theta))
+        finally:
+            lre.lre_destroy(ctx)
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
