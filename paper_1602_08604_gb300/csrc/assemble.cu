@@ -20,7 +20,11 @@
 // Layout after t qubits are done: [P_hi in 4^(n-t)][R_lo in 2^t][C_lo in 2^t],
 // so the final layout (t = n) is rho[R][C].  For n >= 10 the passes are
 // shared-memory tiled (6 qubits, then 4 at a time); smaller n and the
-// leftover qubits use register passes of 1-2 qubits (passes.cuh).
+// leftover qubits use register passes of 1-2 qubits (passes.cuh).  From the
+// tiled first pass on, each block of an intermediate is Hermitian and only
+// its upper half by the low six bits (herm_upper) is stored and read, which
+// cuts the intermediates' traffic by about 40 %; the last pass writes rho
+// whole.
 #include <cuda_runtime.h>
 
 #include "lre_internal.cuh"
@@ -32,11 +36,58 @@ namespace {
 using namespace passes;
 
 // Register pass over J <= 2 qubits: one thread per (P', R_lo, C_lo).
-template <class Num, int J, bool FIRST, bool LAST>
+// The entries of rho the Hermitian-half passes left out (herm_stored false),
+// as the conjugates of their mirrors, one 64 x 64 block (A, B) at a time:
+// the stored entries of block (B, A) that mirror its missing ones -- source
+// row c from column 8 (c / 8 + 1) on, whole sectors -- go through shared
+// memory and come out conjugated and transposed.  Blocks (A, B) and (B, A)
+// read and write disjoint entries, so no two CTAs touch the same place.
+__global__ void __launch_bounds__(256) assemble_mirror(float2 *__restrict__ rho, int64_t d) {
+  __shared__ float2 tile[56][65];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nb = d >> 6;
+  for (int64_t blk = blockIdx.x; blk < nb * nb; blk += gridDim.x) {
+    const int64_t A = blk / nb, B = blk - A * nb;
+    // warp w takes source rows c = w + 8 i (columns 8 (i + 1) .. 63) and target
+    // rows r = 8 + w + 8 i (columns 0 .. 8 (i + 1) - 1): every bound is known
+    // at compile time, so all fourteen loads of a thread are in flight at once
+    const float2 *src = rho + (B * 64) * d + A * 64;  // block (B, A)
+    float2 v[7][2];
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 8 * (i + 1) + lane + 32 * h;
+        if (j < 64) v[i][h] = src[(int64_t)(warp + 8 * i) * d + j];
+      }
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 8 * (i + 1) + lane + 32 * h;
+        if (j < 64) tile[warp + 8 * i][j] = v[i][h];
+      }
+    __syncthreads();
+    float2 *dst = rho + (A * 64) * d + B * 64;        // block (A, B)
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = 8 + warp + 8 * i, c = lane + 32 * h;
+        if (c < 8 * (i + 1)) {
+          const float2 z = tile[c][r];
+          dst[(int64_t)r * d + c] = make_float2(z.x, -z.y);
+        }
+      }
+    __syncthreads();
+  }
+}
+
+template <class Num, int J, bool FIRST, bool LAST, bool HERM>
 __global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
   for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < P.items;
        item += (int64_t)gridDim.x * blockDim.x)
-    asm_item<Num, J, FIRST, LAST>(P, item);
+    asm_item<Num, J, FIRST, LAST, HERM>(P, item);
 }
 
 // ---------------------------------------------------------------------------
@@ -50,7 +101,7 @@ __global__ void __launch_bounds__(256) assemble_pass(AsmParams P) {
 constexpr int TILE_SMEM = ASM_TILE_SMEM;
 
 // First pass: qubits 0..5 of each block of 4096 coefficients ->
-// [R_lo 64][C_lo 64] per block.
+// [R_lo 64][C_lo 64] per block (its stored part, herm_stored).
 template <class Num>
 __global__ void __launch_bounds__(256) assemble_low6(const typename Num::In *__restrict__ in,
                                                     typename Num::V *__restrict__ out, int64_t blocks) {
@@ -58,12 +109,16 @@ __global__ void __launch_bounds__(256) assemble_low6(const typename Num::In *__r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V *S = reinterpret_cast<V *>(smem_raw);  // 4096 + 256 padded entries
   for (int64_t blk = blockIdx.x; blk < blocks; blk += gridDim.x)
-    asm_low6_block<Num, false>(in, out, blk, S, LastScale{0.f, 0.f});
+    asm_low6_block<Num, false, true>(in, out, blk, S, LastScale{0.f, 0.f});
 }
 
 // 4-qubit pass over qubits t..t+3 (t >= 6): unit = (P', R_lo, 16 consecutive
 // C_lo).  Input [P'][p 256][R_lo][C_lo]; output [P'][R'][C'] with
-// R' = (rJ << t) | R_lo, C' = (cJ << t) | C_lo.
+// R' = (rJ << t) | R_lo, C' = (cJ << t) | C_lo.  Only the stored part is
+// read and written (herm_stored): a strip whose 16 columns all lie outside it
+// is skipped, a straddling strip is computed whole (its other columns read and
+// write places nobody reads), and the last pass writes the stored entries of
+// rho only (assemble_mirror fills the rest).
 template <class Num, bool LAST>
 __global__ void __launch_bounds__(256) assemble_high4(const typename Num::V *__restrict__ in,
                                                      void *__restrict__ out, int t, int64_t units,
@@ -80,6 +135,7 @@ __global__ void __launch_bounds__(256) assemble_high4(const typename Num::V *__r
     const int64_t Pp = u / per_p;
     const int64_t L0 = (u - Pp * per_p) * 16;  // first L of the strip
     const int64_t R_lo = L0 >> t, C0 = L0 & (side - 1);
+    if ((C0 & 63) + 15 < ((R_lo & 63) & ~7)) continue;  // no column of the strip is stored
     const V *src = in + Pp * 256 * L4 + L0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -106,22 +162,27 @@ __global__ void __launch_bounds__(256) assemble_high4(const typename Num::V *__r
       const int r2 = (w >> 1) & 1, c2 = w & 1, r3 = (w >> 3) & 1, c3 = (w >> 2) & 1;
       const int64_t rJ = r0 | (r1 << 1) | (r2 << 2) | (r3 << 3);
       const int64_t cJ = c0 | (c1 << 1) | (c2 << 2) | (c3 << 3);
-      const int64_t o = Pp * W * W + ((rJ << t) | R_lo) * W + ((cJ << t) | (C0 + l));
-      if constexpr (LAST)
-        static_cast<float2 *>(out)[o] = to_c64(v[w], scale);
-      else
+      const int64_t Rp = (rJ << t) | R_lo, Cp = (cJ << t) | (C0 + l);
+      const int64_t o = Pp * W * W + Rp * W + Cp;
+      if constexpr (LAST) {
+        if (herm_stored(R_lo, C0 + l)) static_cast<float2 *>(out)[o] = to_c64(v[w], scale);
+      } else {
         static_cast<V *>(out)[o] = v[w];
+      }
     }
     __syncthreads();
   }
 }
 
+// herm: the pass runs after the tiled first pass, on the stored half only
 template <class Num, int J>
-void launch_reg(bool first, bool last, const AsmParams &p, int grid, cudaStream_t s) {
-  if (first && last) assemble_pass<Num, J, true, true><<<grid, 256, 0, s>>>(p);
-  else if (first) assemble_pass<Num, J, true, false><<<grid, 256, 0, s>>>(p);
-  else if (last) assemble_pass<Num, J, false, true><<<grid, 256, 0, s>>>(p);
-  else assemble_pass<Num, J, false, false><<<grid, 256, 0, s>>>(p);
+void launch_reg(bool first, bool last, bool herm, const AsmParams &p, int grid, cudaStream_t s) {
+  if (first && last) assemble_pass<Num, J, true, true, false><<<grid, 256, 0, s>>>(p);
+  else if (first) assemble_pass<Num, J, true, false, false><<<grid, 256, 0, s>>>(p);
+  else if (last && herm) assemble_pass<Num, J, false, true, true><<<grid, 256, 0, s>>>(p);
+  else if (last) assemble_pass<Num, J, false, true, false><<<grid, 256, 0, s>>>(p);
+  else if (herm) assemble_pass<Num, J, false, false, true><<<grid, 256, 0, s>>>(p);
+  else assemble_pass<Num, J, false, false, false><<<grid, 256, 0, s>>>(p);
 }
 
 template <class Num>
@@ -184,14 +245,26 @@ lre_status run_passes(lre_ctx *ctx, const typename Num::In *in0, int n, lre_c64 
     if (blocks > cap) blocks = cap;
     {
       Launch L(ctx, last ? "assemble_last" : "assemble_pass", s);
-      if (J == 2) launch_reg<Num, 2>(first, last, p, (int)blocks, s);
-      else launch_reg<Num, 1>(first, last, p, (int)blocks, s);
+      const bool herm = n >= 10;  // after the tiled first pass: the stored part only
+      if (J == 2) launch_reg<Num, 2>(first, last, herm, p, (int)blocks, s);
+      else launch_reg<Num, 1>(first, last, herm, p, (int)blocks, s);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble pass launch");
     in = p.out;
     t += J;
     ++k;
+  }
+  if (n >= 10) {  // the Hermitian-half passes wrote the stored entries of rho only
+    const int64_t nb = 1ll << (n - 6);
+    int64_t g = (int64_t)ctx->num_sms * 8;
+    if (g > nb * nb) g = nb * nb;
+    {
+      Launch L(ctx, "assemble_mirror", s);
+      assemble_mirror<<<(int)g, 256, 0, s>>>(reinterpret_cast<float2 *>(rho), 1ll << n);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "assemble_mirror launch");
   }
   return LRE_OK;
 }
@@ -220,14 +293,19 @@ lre_status assemble_preload() {
       reinterpret_cast<const void *>(assemble_low6<NumF64>),
       reinterpret_cast<const void *>(assemble_high4<NumF64, true>),
       reinterpret_cast<const void *>(assemble_high4<NumF64, false>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, true, true>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, true, false>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, true>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, false>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, true, true>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, true, false>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, true>),
-      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, false>)};
+      reinterpret_cast<const void *>(assemble_mirror),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, true, true, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, true, false, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, true, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, false, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, true, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 1, false, false, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, true, true, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, true, false, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, true, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, false, false>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, true, true>),
+      reinterpret_cast<const void *>(assemble_pass<NumF64, 2, false, false, true>)};
   for (const void *k : kernels) {
     cudaFuncAttributes attr;
     if (cudaFuncGetAttributes(&attr, k) != cudaSuccess) return LRE_ERR_CUDA;

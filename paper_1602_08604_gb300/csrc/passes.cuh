@@ -378,8 +378,21 @@ struct AsmParams {
   LastScale scale;
 };
 
+// Hermitian half (HERM, passes after the first six qubits): every block of
+// the assembly's intermediates, fixed higher letters over the transformed
+// qubits, is Hermitian (real coefficients times tensor products of Hermitian
+// Paulis), so only the stored entries are written and read: those whose low
+// six column bits are at least the low six row bits rounded down to a
+// multiple of 8 (whole 128-byte lines of the 16-byte intermediates, whole
+// sectors of rho).  A pass's outputs keep the low bits of its inputs, so the
+// set carries through, and the mirror (C, R) of every entry left out is
+// stored.  The last pass writes the stored entries of rho and assemble_mirror
+// the rest, as conjugates (the mirror of an exact butterfly is exactly the
+// conjugate).
+__device__ __forceinline__ bool herm_stored(int64_t R, int64_t C) { return (C & 63) >= ((R & 63) & ~7); }
+
 // One (P', R_lo, C_lo) item of an assembly pass over J <= 2 qubits.
-template <class Num, int J, bool FIRST, bool LAST>
+template <class Num, int J, bool FIRST, bool LAST, bool HERM = false>
 __device__ __forceinline__ void asm_item(const AsmParams &P, int64_t item) {
   using V = typename Num::V;
   constexpr int NP = 1 << (2 * J);
@@ -389,6 +402,7 @@ __device__ __forceinline__ void asm_item(const AsmParams &P, int64_t item) {
   const int64_t L = item & (L4 - 1);
   const int64_t Pp = item >> (2 * t);
   const int64_t R_lo = L >> t, C_lo = L & ((1ll << t) - 1);
+  if (HERM && !herm_stored(R_lo, C_lo)) return;  // not stored: its mirror carries it
   V v[NP];
   const int64_t ibase = Pp * NP * L4 + L;
 #pragma unroll
@@ -464,17 +478,13 @@ __device__ __forceinline__ void m2(V (&v)[16]) {
 // shared tile S (4096 + 256 entries).  All 256 threads of the CTA call it
 // together.  LAST: the block is the whole matrix (n = 6) and is written as
 // complex64 with the final scale.
-template <class Num, bool LAST>
-__device__ __forceinline__ void asm_low6_block(const typename Num::In *__restrict__ in, void *__restrict__ out,
-                                               int64_t blk, typename Num::V *S, const LastScale &scale) {
+// asm_low6_finish: the same after S holds the block's coefficients (and the
+// CTA has synchronised): the butterflies and the writes.
+template <class Num, bool LAST, bool HERM = false>
+__device__ __forceinline__ void asm_low6_finish(void *__restrict__ out, int64_t blk, typename Num::V *S,
+                                                const LastScale &scale) {
   using V = typename Num::V;
   const int tid = threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int i = tid + 256 * k;
-    S[pad16(i)] = load_first(in, blk * 4096 + i);
-  }
-  __syncthreads();
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int sh = 4 * r;
@@ -497,10 +507,23 @@ __device__ __forceinline__ void asm_low6_block(const typename Num::In *__restric
     for (int q = 0; q < 6; ++q) pos |= ((((R >> q) & 1) << 1) | ((C >> q) & 1)) << (2 * q);
     if constexpr (LAST)
       static_cast<float2 *>(out)[blk * 4096 + o] = to_c64(S[pad16(pos)], scale);
-    else
+    else if (!HERM || herm_stored(R, C))  // HERM: the stored part of the 64 x 64 block
       static_cast<V *>(out)[blk * 4096 + o] = S[pad16(pos)];
   }
   __syncthreads();
+}
+
+template <class Num, bool LAST, bool HERM = false>
+__device__ __forceinline__ void asm_low6_block(const typename Num::In *__restrict__ in, void *__restrict__ out,
+                                               int64_t blk, typename Num::V *S, const LastScale &scale) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int i = tid + 256 * k;
+    S[pad16(i)] = load_first(in, blk * 4096 + i);
+  }
+  __syncthreads();
+  asm_low6_finish<Num, LAST, HERM>(out, blk, S, scale);
 }
 
 }  // namespace passes

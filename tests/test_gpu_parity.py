@@ -248,16 +248,30 @@ def test_estimate_host_matches_device_path(env, n, kind, chunk):
     assert rel_fro(rh.numpy(), direct.mu(t_ref, n)) <= 1e-6
 
 
-@pytest.mark.parametrize("n", [10, 11, 12, 13])
-def test_assemble_tiled_passes_sampled(env, n):
-    """n >= 10 uses the shared-memory tiled passes (6 + 4 + ... qubits)."""
+@pytest.mark.parametrize("n,shift", [(10, 0), (11, 0), (12, 0), (13, 0), (10, 1), (12, 1)])
+def test_assemble_tiled_passes_sampled(env, n, shift):
+    """n >= 10 uses the shared-memory tiled passes (6 + 4 + ... qubits) on the
+    Hermitian half, and a mirror pass for the rest of rho; shift = 1 hands
+    theta over at an address that is 8 but not 16 bytes aligned: the same
+    bits."""
     torch, lre, ctx = env
     rng = np.random.default_rng(500 + n)
     t = rng.uniform(-1, 1, 4 ** n)
     t[0] = 1.0
     d = 2 ** n
     rho = torch.empty((d, d), dtype=torch.complex64, device="cuda")
-    lre.lre_assemble(ctx, torch.from_numpy(t).cuda(), n, rho)
+    if shift:
+        buf = torch.empty(4 ** n + 2, dtype=torch.float64, device="cuda")
+        th = buf[1:1 + 4 ** n]
+        assert th.data_ptr() % 16 == 8
+        th.copy_(torch.from_numpy(t))
+        lre.lre_assemble(ctx, th, n, rho)
+        aligned = torch.empty_like(rho)
+        lre.lre_assemble(ctx, torch.from_numpy(t).cuda(), n, aligned)
+        lre.lre_sync(ctx)
+        assert torch.equal(rho, aligned)
+    else:
+        lre.lre_assemble(ctx, torch.from_numpy(t).cuda(), n, rho)
     lre.lre_sync(ctx)
     r = rng.integers(0, d, 300)
     c = rng.integers(0, d, 300)
