@@ -655,7 +655,8 @@ bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, const void *b
     if (i + 1 < rank) st[i] = strides[i];
   }
   CUresult r = enc(map, type, rank, const_cast<void *>(base), d, st, bx, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -898,6 +899,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
         gp.up3[id] = id <= a.n ? ipow(3, a.n - id) : 0;
       }
       gp.status = ctx->d_status;
+      gp.hi_from = planes_hi_from(a.shots_uniform);
       const int in_t = (planes && k == 1) ? (int)T_I24P : pp.in_t;
       lre_status tst = ctx->generic_tma ? tma_pass(ctx, gp, pp.J, in_t, pp.acc_t, pp.mode, pp.weight, s)
                                         : LRE_ERR_UNSUPPORTED;

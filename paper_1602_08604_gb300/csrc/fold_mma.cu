@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     const int pair = (warp - 4) >> 1;
     const int quarter = warp & 3;
     const int plA = (quarter & 1) * 32 + lane;
+    const int hi_from = planes_hi_from(shots);  // split planes: identities from which the high plane counts
     const float scale = BIASED ? 1.f : 16777216.f;
     const int32_t sub = BIASED && plA == 0 ? BIAS : 0;
     int pend = -1;  // F9: ring slot of this warp's last tile, written but not yet counted
@@ -604,11 +605,18 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
       } else if (out_hi) {  // split planes: low 16 bits, then the (signed) bits above
         unsigned short *lo = reinterpret_cast<unsigned short *>(out) + tile * 4096 + plA;
         signed char *hi = reinterpret_cast<signed char *>(out_hi) + tile * 4096 + plA;
+        bool bad = false;  // a partial the planes cannot hold: a row above its shots
 #pragma unroll
         for (int p = 0; p < 64; ++p) {
           __stcs(lo + p * 64, (unsigned short)(acc[p] & 0xFFFF));
-          __stcs(hi + p * 64, (signed char)(acc[p] >> 16));
+          if (planes_hi_needed((int64_t)p * 64 + (quarter & 1) * 32, hi_from)) {  // warp-uniform
+            __stcs(hi + p * 64, (signed char)(acc[p] >> 16));
+            bad |= acc[p] >= (1 << 23) || acc[p] < -(1 << 23);
+          } else {
+            bad |= acc[p] != (int32_t)(int16_t)acc[p];
+          }
         }
+        if (bad) latch(status, LRE_ERR_SHOTS_MISMATCH);
       } else {
         int32_t *o = out + tile * 4096 + plA;
 #pragma unroll

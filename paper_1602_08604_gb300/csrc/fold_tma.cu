@@ -74,6 +74,11 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
   const int64_t tasks = P.items / TC;  // items = 3^(r-J) 2^(r-J) C
   const int64_t stride = (int64_t)gridDim.x * TMA_WARPS;
   const int64_t first = (int64_t)blockIdx.x * TMA_WARPS + warp;
+  // PLANES: both boxes of every task are loaded (neighbouring tasks then run
+  // in step and share the 256-byte L2 lines of both planes), but the high
+  // plane holds values only where one of a task's letters can need it; the
+  // others take the low 16 bits as int16
+  auto with_hi = [&](int64_t task) { return PLANES && planes_hi_needed((task % cblocks) * TC, P.hi_from); };
   auto issue = [&](int64_t task, int b) {
     const int64_t ahoh = task / cblocks, cb = task - ahoh * cblocks;
     const int64_t ah = ahoh / P.n_oh, oh = ahoh - ah * P.n_oh;
@@ -101,6 +106,7 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
     const int32_t *S = reinterpret_cast<const int32_t *>(buf + b * BOX);
     const unsigned short *SL = reinterpret_cast<const unsigned short *>(buf + b * BOX);
     const signed char *SH = reinterpret_cast<const signed char *>(buf + b * BOX + BOX_LO);
+    const bool hi = with_hi(task);
     AccT acc[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) acc[p] = 0;
@@ -111,7 +117,8 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
       for (int ol = 0; ol < NO; ++ol) {
         const int idx = (al * NO + ol) * TC + lane;
         if constexpr (PLANES)
-          v[ol] = (AccT)(int32_t)(((uint32_t)(int32_t)SH[idx] << 16) | (uint32_t)SL[idx]);
+          v[ol] = hi ? (AccT)(int32_t)(((uint32_t)(int32_t)SH[idx] << 16) | (uint32_t)SL[idx])
+                     : (AccT)(int16_t)SL[idx];
         else
           v[ol] = (AccT)S[idx];
       }

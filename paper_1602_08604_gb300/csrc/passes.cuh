@@ -142,7 +142,30 @@ struct GenParams {
   int64_t dint[16];      // N 3^k as an integer (uniform shots)
   double recip[16];      // correctly rounded 1 / denom[k]
   int64_t up3[16];       // 3^(n-k)
+  int hi_from;           // split-plane input: see planes_hi_needed
 };
+
+// Split-plane partials of the tensor-core first pass: the partial of a letter
+// with k identities among its six qubits is at most shots 3^k in magnitude
+// (each basis row sums to the shots), so its high plane (bits 16..23) is
+// needed only from k = hi_from on, the least k with shots 3^k > 32767; below
+// that the low 16 bits, read as int16, are the value.  Letters are numbered
+// plB * 64 + plA (three letters each, 2 bits a letter, 0 = I) and a run of 32
+// from c0 (a multiple of 32) fixes plB and the top bit of plA's third
+// letter: its most identities are those of plB plus 3 (lower half, that
+// letter I or X) or 2 (upper half, Y or Z).  The high plane of such a run is
+// written only when one of its letters can need it, and read as values only
+// then (the reader loads every run's bytes: whole L2 lines stream faster).
+__host__ __device__ inline int planes_hi_from(int64_t shots) {
+  int k = 0;
+  for (int64_t b = shots; k < 7 && b <= 32767; ++k) b *= 3;
+  return k;
+}
+__host__ __device__ inline bool planes_hi_needed(int64_t c0, int hi_from) {
+  const int plB = (int)((c0 >> 6) & 63), half = (int)((c0 >> 5) & 1);
+  const int idc = ((plB & 3) == 0) + (((plB >> 2) & 3) == 0) + (((plB >> 4) & 3) == 0);
+  return idc + (half ? 2 : 3) >= hi_from;
+}
 
 // Loads of pass inputs: the read-only path, or (COHERENT) straight from L2 for
 // inputs written earlier by the same kernel launch (the batched kernel).

@@ -180,3 +180,24 @@ def test_rows_off_their_shots_within_range_match_oracle(dtype, shots):
             np.testing.assert_array_equal(theta.cpu().numpy(), want)
         finally:
             lre.lre_destroy(ctx)
+
+
+def test_split_planes_refuse_a_row_above_its_shots():
+    """The split-plane partials store the high plane only where a partial can
+    exceed int16 when every basis row sums to its shots.  A row holding 16
+    times its shots (every count still within [0, shots], the grand total
+    kept by emptying other rows) gives the letter I I I X X X a partial of
+    42000 in a run without high planes: the tensor path latches
+    LRE_ERR_SHOTS_MISMATCH instead of returning a wrong theta."""
+    torch = need_gpu()
+    n, shots = 10, 1000
+    raw = np.zeros((3 ** n, 2 ** n), dtype=np.int64)
+    raw[:, 0] = shots                                  # every row: all shots on outcome 0
+    o = np.arange(64)
+    even = np.array([bin((x >> 3) & 7).count("1") % 2 == 0 for x in o])
+    raw[0, :] = 0
+    raw[0, o[even]] = 500                              # 32 outcomes x 500 = 16 x the shots
+    excess = int(raw[0].sum()) - shots
+    raw[3 ** n - 1 - np.arange(excess // shots), 0] = 0  # the total stays shots * 3^n
+    assert raw.sum() == shots * 3 ** n and raw.max() <= shots
+    _bad_estimate(torch, raw.astype(np.int16), shots, n, 0)
