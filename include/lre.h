@@ -205,10 +205,12 @@ lre_status lre_assemble(lre_ctx *ctx, const double *theta, int n, lre_c64 *rho, 
 lre_status lre_assemble_noalloc(const double *theta, int n, lre_c64 *rho, lre_stream stream);
 
 /* Step (iii): rho_out = argmin over density matrices sigma of
- * ||sigma - rho_in||_F (Sec. II, Smolin et al.): FP64 Hermitian
- * eigendecomposition of rho_in (promoted to complex128), the eigenvalue
- * correction onto the probability simplex, and the reconstruction in FP64
- * rounded once to complex64.  rho_in, rho_out: device complex64
+ * ||sigma - rho_in||_F (Sec. II, Smolin et al.): the eigenpairs of rho_in
+ * on the needed side of the threshold (Lanczos with FP64 vectors, its
+ * product with rho_in in double-float arithmetic, certified; else an FP64
+ * Hermitian eigendecomposition of rho_in promoted to complex128), the
+ * eigenvalue correction onto the probability simplex, and the
+ * reconstruction in FP64 rounded once to complex64.  rho_in, rho_out: device complex64
  * [2^n][2^n] (may alias); eig_mu, eig_rho: device FP64 [2^n] or NULL,
  * receiving the spectra of rho_in and rho_out in decreasing order.  The call
  * synchronises `stream` once (to size the reconstruction). */

@@ -1,6 +1,7 @@
 // Step (iii) without the O(d^3) reduction: the Smolin et al. projection of
 // Sec. II needs only the eigenpairs on one side of its threshold, so they are
-// computed by the Lanczos method in FP64 with full reorthogonalisation, on
+// computed by the Lanczos method (FP64 vectors and scalars, the product with
+// mu in double-float arithmetic) with full reorthogonalisation, on
 // hand-written kernels (matrix-vector product, Gram-Schmidt projections,
 // norms, Ritz vectors), and the small tridiagonal problem is solved by the
 // bisection and inverse-iteration kernels of tridiag.cu.
@@ -25,10 +26,11 @@
 // fallback also runs when r is not decided within KRYLOV_MAX steps.
 //
 // Layout: mu (row-major complex64) is promoted once to complex128 M (the
-// same row-major order); the Krylov basis Q holds one d-vector per row
-// (vector t at Q + t d).  y = M x is the row-major product, so the vectors
-// are eigenvectors of mu; the rebuild of project.cu works on conj(mu), whose
-// eigenvectors are their conjugates.
+// same row-major order; the rebuild's working matrix, its norm and trace),
+// while the Lanczos product reads the complex64 input itself; the Krylov
+// basis Q holds one d-vector per row (vector t at Q + t d).  y = mu x is the
+// row-major product, so the vectors are eigenvectors of mu; the rebuild of
+// project.cu works on conj(mu), whose eigenvectors are their conjugates.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,7 +43,7 @@
 namespace lre {
 namespace {
 
-constexpr int MV_ROWS = 16;        // rows of M per CTA of the product (two per warp)
+constexpr int MV_RPW = 1;          // rows of M per warp of the product (eight warps per CTA)
 constexpr int MV_CHUNK = 1024;     // x entries staged in shared memory at a time
 constexpr int RED_THREADS = 256;
 
@@ -51,47 +53,74 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// y = M x (M row-major d x d complex128, d a multiple of MV_CHUNK or d <
-// MV_CHUNK).  Each warp holds two rows' sums; x is staged in shared memory.
-__global__ void __launch_bounds__(256) kry_matvec(const double2 *__restrict__ M, const double2 *__restrict__ x,
-                                                  double2 *__restrict__ y, int64_t d) {
-  __shared__ double2 xs[MV_CHUNK];
+// ---- the Lanczos product y = mu x in double-float arithmetic on the FP32 pipes --
+// mu arrives as complex64, so its entries are exact FP32 numbers; with x held
+// as two FP32 parts (x = xh + xl, |x - xh - xl| about 2^-48 |x|), each real
+// product m x is p = RN(m xh) plus its exact error e = fma(m, xh, -p) plus
+// m xl, and the row sums are kept as unevaluated FP32 pairs (sh, sl) with
+// Knuth's TwoSum on the leading part: about 2^-44 relative per term, against
+// 2^-53 in FP64 -- far inside the Lanczos tolerances -- at the FP32 rate,
+// where GB300's FP64 rate had made the product FP64-bound, and reading 8
+// bytes per entry of mu instead of 16.  The _rn intrinsics keep the compiler
+// from contracting the steps into FMAs, which would break the exact errors.
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float m, float xh, float xl) {
+  const float p = __fmul_rn(m, xh);
+  const float e = __fmaf_rn(m, xh, -p);
+  const float t = __fadd_rn(sh, p);  // TwoSum(sh, p) = t + err exactly
+  const float bp = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(m, xl, e)));
+}
+
+// x (complex128) -> {re hi, re lo, im hi, im lo} as FP32
+__global__ void kry_split(const double2 *__restrict__ x, float4 *__restrict__ xs, int64_t d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    xs[i] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+  }
+}
+
+// y = M x with M the row-major d x d complex64 matrix, x split by kry_split;
+// MV_RPW rows per warp (each staged x entry serves them all), x staged in
+// shared memory (d a multiple of MV_CHUNK or d < MV_CHUNK), the warp's partial
+// sums added in FP64 at the end.
+template <int RPW>
+__global__ void __launch_bounds__(256) kry_matvec_df(const float2 *__restrict__ M, const float4 *__restrict__ xsplit,
+                                                     double2 *__restrict__ y, int64_t d) {
+  __shared__ float4 xs[MV_CHUNK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r0 = (int64_t)blockIdx.x * MV_ROWS + 2 * warp;
-  double ar = 0, ai = 0, br = 0, bi = 0;
+  const int64_t r0 = ((int64_t)blockIdx.x * 8 + warp) * RPW;
+  float rh[RPW], rl[RPW], ih[RPW], il[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) rh[r] = rl[r] = ih[r] = il[r] = 0.f;
   const int64_t chunk = d < MV_CHUNK ? d : MV_CHUNK;
   for (int64_t c0 = 0; c0 < d; c0 += chunk) {
     __syncthreads();
-    for (int k = threadIdx.x; k < chunk; k += blockDim.x) xs[k] = x[c0 + k];
+    for (int k = threadIdx.x; k < chunk; k += blockDim.x) xs[k] = xsplit[c0 + k];
     __syncthreads();
     if (r0 < d) {
-      const double2 *ra = M + r0 * d + c0;
-      const double2 *rb = ra + d;
-      const bool two = r0 + 1 < d;
+      const float2 *row = M + r0 * d + c0;
       for (int k = lane; k < chunk; k += 32) {
-        const double2 xv = xs[k];
-        const double2 u = ra[k];
-        ar = fma(u.x, xv.x, ar);
-        ar = fma(-u.y, xv.y, ar);
-        ai = fma(u.x, xv.y, ai);
-        ai = fma(u.y, xv.x, ai);
-        if (two) {
-          const double2 v = rb[k];
-          br = fma(v.x, xv.x, br);
-          br = fma(-v.y, xv.y, br);
-          bi = fma(v.x, xv.y, bi);
-          bi = fma(v.y, xv.x, bi);
+        const float4 xv = xs[k];  // x re = xv.x + xv.y, x im = xv.z + xv.w
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+          if (r0 + r < d) {
+            const float2 u = row[(int64_t)r * d + k];
+            df_mac(rh[r], rl[r], u.x, xv.x, xv.y);   // re += ur xr - ui xi
+            df_mac(rh[r], rl[r], -u.y, xv.z, xv.w);
+            df_mac(ih[r], il[r], u.x, xv.z, xv.w);   // im += ur xi + ui xr
+            df_mac(ih[r], il[r], u.y, xv.x, xv.y);
+          }
         }
       }
     }
   }
-  ar = warp_sum(ar);
-  ai = warp_sum(ai);
-  br = warp_sum(br);
-  bi = warp_sum(bi);
-  if (lane == 0 && r0 < d) {
-    y[r0] = make_double2(ar, ai);
-    if (r0 + 1 < d) y[r0 + 1] = make_double2(br, bi);
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const double re = warp_sum((double)rh[r] + (double)rl[r]), im = warp_sum((double)ih[r] + (double)il[r]);
+    if (lane == 0 && r0 + r < d) y[r0 + r] = make_double2(re, im);
   }
 }
 
@@ -302,6 +331,8 @@ __global__ void kry_eig_rho(const double *w_asc, int64_t r, double shift, double
 
 struct KryBuffers {
   double2 *M, *Q, *W, *h1, *h2, *Z;
+  const float2 *M32;  // the complex64 input, read by the double-float product
+  float4 *Xs;         // the current Lanczos vector split for it
   double *alpha, *beta, *b2, *stats, *Wr, *Xr, *lu, *last, *nrm;
   int *cl, *nclust, *breakdown;
   SmolinResult *res;
@@ -381,7 +412,8 @@ lre_status lanczos_steps(lre_ctx *ctx, const KryBuffers &B, int64_t d, int64_t b
     const int cols = (int)(c + 1);
     {
       Launch L(ctx, "kry_matvec", s);
-      kry_matvec<<<(unsigned)((d + MV_ROWS - 1) / MV_ROWS), 256, 0, s>>>(B.M, B.Q + c * d, B.W, d);
+      kry_split<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(B.Q + c * d, B.Xs, d);
+      kry_matvec_df<MV_RPW><<<(unsigned)((d + 8 * MV_RPW - 1) / (8 * MV_RPW)), 256, 0, s>>>(B.M32, B.Xs, B.W, d);
     }
     {
       Launch L(ctx, "kry_reorth", s, 4);
@@ -442,7 +474,7 @@ lre_status project_krylov(lre_ctx *ctx, cublasContext *blas, const lre_c64 *rho_
                       u(4 * sizeof(double)) + u((size_t)B.ct_max * sizeof(double)) +
                       u((size_t)B.rows * B.ct_max * sizeof(double)) + u((size_t)5 * B.rows * B.ct_max * sizeof(double)) +
                       u((size_t)B.ct_max * sizeof(double)) + u(sizeof(double)) + u((size_t)(B.ct_max + 2) * sizeof(int)) +
-                      3 * 256 + 2 * u((size_t)KRY_VERIFY * sizeof(double)) + 1024;
+                      3 * 256 + 2 * u((size_t)KRY_VERIFY * sizeof(double)) + u((size_t)d * sizeof(float4)) + 1024;
   lre_status st = ensure_workspace(ctx, need);
   if (st != LRE_OK) return st;
   char *p = static_cast<char *>(ctx->ws);
@@ -472,6 +504,8 @@ lre_status project_krylov(lre_ctx *ctx, cublasContext *blas, const lre_c64 *rho_
   B.res = reinterpret_cast<SmolinResult *>(take(sizeof(SmolinResult)));
   double *alpha2 = reinterpret_cast<double *>(take((size_t)KRY_VERIFY * sizeof(double)));
   double *beta2 = reinterpret_cast<double *>(take((size_t)KRY_VERIFY * sizeof(double)));
+  B.Xs = reinterpret_cast<float4 *>(take((size_t)d * sizeof(float4)));
+  B.M32 = reinterpret_cast<const float2 *>(rho_in);  // unchanged until the rebuild writes rho_out
 
   const int grid = ctx->num_sms * 8;
   {
