@@ -411,7 +411,7 @@ lre_status lanczos_steps(lre_ctx *ctx, const KryBuffers &B, int64_t d, int64_t b
     const int64_t c = base + j;  // the row of q_j
     const int cols = (int)(c + 1);
     {
-      Launch L(ctx, "kry_matvec", s);
+      Launch L(ctx, "kry_matvec", s, 2);  // the split and the product
       kry_split<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(B.Q + c * d, B.Xs, d);
       kry_matvec_df<MV_RPW><<<(unsigned)((d + 8 * MV_RPW - 1) / (8 * MV_RPW)), 256, 0, s>>>(B.M32, B.Xs, B.W, d);
     }
