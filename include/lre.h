@@ -206,8 +206,8 @@ lre_status lre_assemble_noalloc(const double *theta, int n, lre_c64 *rho, lre_st
 
 /* Step (iii): rho_out = argmin over density matrices sigma of
  * ||sigma - rho_in||_F (Sec. II, Smolin et al.): the eigenpairs of rho_in
- * on the needed side of the threshold (Lanczos with FP64 vectors, its
- * product with rho_in in double-float arithmetic, certified; else an FP64
+ * on the needed side of the threshold (Lanczos in double-float arithmetic
+ * with FP64 scalars, certified; else an FP64
  * Hermitian eigendecomposition of rho_in promoted to complex128), the
  * eigenvalue correction onto the probability simplex, and the
  * reconstruction in FP64 rounded once to complex64.  rho_in, rho_out: device complex64

@@ -1,7 +1,8 @@
 // Step (iii) without the O(d^3) reduction: the Smolin et al. projection of
 // Sec. II needs only the eigenpairs on one side of its threshold, so they are
-// computed by the Lanczos method (FP64 vectors and scalars, the product with
-// mu in double-float arithmetic) with full reorthogonalisation, on
+// computed by the Lanczos method (FP64 scalars and work vector; the basis as
+// FP32 pairs, the product with mu and the reorthogonalisation in double-float
+// arithmetic) with full reorthogonalisation, on
 // hand-written kernels (matrix-vector product, Gram-Schmidt projections,
 // norms, Ritz vectors), and the small tridiagonal problem is solved by the
 // bisection and inverse-iteration kernels of tridiag.cu.
@@ -28,7 +29,7 @@
 // Layout: mu (row-major complex64) is promoted once to complex128 M (the
 // same row-major order; the rebuild's working matrix, its norm and trace),
 // while the Lanczos product reads the complex64 input itself; the Krylov
-// basis Q holds one d-vector per row (vector t at Q + t d).  y = mu x is the
+// basis Q holds one d-vector per row (vector t at Q + t d) as FP32 pairs.  y = mu x is the
 // row-major product, so the vectors are eigenvectors of mu; the rebuild of
 // project.cu works on conj(mu), whose eigenvectors are their conjugates.
 #include <cuda_runtime.h>
@@ -73,13 +74,33 @@ __device__ __forceinline__ void df_mac(float &sh, float &sl, float m, float xh, 
   sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(m, xl, e)));
 }
 
-// x (complex128) -> {re hi, re lo, im hi, im lo} as FP32
+// The same for a product of two such pairs, (ah + al)(bh + bl): the leading
+// product exactly (p and its error), the cross terms into the error part.
+__device__ __forceinline__ void df_mac2(float &sh, float &sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float t = __fadd_rn(sh, p);
+  const float bp = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// complex128 <-> {re hi, re lo, im hi, im lo} as FP32 (the Krylov basis, the
+// split copies of the work vector): about 2^-48 relative per component
+__device__ __forceinline__ float4 df_split(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 df_join(float4 q) {
+  return make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+}
+
 __global__ void kry_split(const double2 *__restrict__ x, float4 *__restrict__ xs, int64_t d) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = x[i];
-    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-    xs[i] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x)
+    xs[i] = df_split(x[i]);
 }
 
 // y = M x with M the row-major d x d complex64 matrix, x split by kry_split;
@@ -88,7 +109,8 @@ __global__ void kry_split(const double2 *__restrict__ x, float4 *__restrict__ xs
 // sums added in FP64 at the end.
 template <int RPW>
 __global__ void __launch_bounds__(256) kry_matvec_df(const float2 *__restrict__ M, const float4 *__restrict__ xsplit,
-                                                     double2 *__restrict__ y, int64_t d) {
+                                                     double2 *__restrict__ y, float4 *__restrict__ ysplit,
+                                                     int64_t d) {
   __shared__ float4 xs[MV_CHUNK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = ((int64_t)blockIdx.x * 8 + warp) * RPW;
@@ -120,27 +142,31 @@ __global__ void __launch_bounds__(256) kry_matvec_df(const float2 *__restrict__ 
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const double re = warp_sum((double)rh[r] + (double)rl[r]), im = warp_sum((double)ih[r] + (double)il[r]);
-    if (lane == 0 && r0 + r < d) y[r0 + r] = make_double2(re, im);
+    if (lane == 0 && r0 + r < d) {
+      y[r0 + r] = make_double2(re, im);
+      ysplit[r0 + r] = df_split(make_double2(re, im));
+    }
   }
 }
 
-// h[t] = q_t^dag w for t < m (one CTA per vector).
-__global__ void __launch_bounds__(RED_THREADS) kry_dots(const double2 *__restrict__ Q, int m,
-                                                        const double2 *__restrict__ w, double2 *__restrict__ h,
+// h[t] = q_t^dag w for t < m (one CTA per vector), the basis rows and w in
+// split form, products and sums in double-float, the partial sums added in
+// FP64.
+__global__ void __launch_bounds__(RED_THREADS) kry_dots(const float4 *__restrict__ Q, int m,
+                                                        const float4 *__restrict__ w, double2 *__restrict__ h,
                                                         int64_t d) {
   __shared__ double sr[RED_THREADS / 32], si[RED_THREADS / 32];
   for (int t = blockIdx.x; t < m; t += gridDim.x) {
-    const double2 *q = Q + (int64_t)t * d;
-    double re = 0, im = 0;
+    const float4 *q = Q + (int64_t)t * d;
+    float rh = 0, rl = 0, ih = 0, il = 0;
     for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
-      const double2 a = q[i], b = w[i];
-      re = fma(a.x, b.x, re);
-      re = fma(a.y, b.y, re);  // conj(a) b
-      im = fma(a.x, b.y, im);
-      im = fma(-a.y, b.x, im);
+      const float4 a = q[i], b = w[i];  // conj(a) b
+      df_mac2(rh, rl, a.x, a.y, b.x, b.y);
+      df_mac2(rh, rl, a.z, a.w, b.z, b.w);
+      df_mac2(ih, il, a.x, a.y, b.z, b.w);
+      df_mac2(ih, il, -a.z, -a.w, b.x, b.y);
     }
-    re = warp_sum(re);
-    im = warp_sum(im);
+    const double re = warp_sum((double)rh + (double)rl), im = warp_sum((double)ih + (double)il);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
       sr[warp] = re;
@@ -159,26 +185,48 @@ __global__ void __launch_bounds__(RED_THREADS) kry_dots(const double2 *__restric
   }
 }
 
-// w -= sum_{t < m} h[t] q_t; h staged in shared memory (dynamic, m entries).
-__global__ void __launch_bounds__(256) kry_update(double2 *__restrict__ w, const double2 *__restrict__ Q, int m,
+// w -= sum_{t < m} h[t] q_t (basis rows in split form, h split into shared
+// memory; dynamic shared memory m float4), and ws = the split w.  A CTA
+// takes 64 entries of w; its four warp pairs sum over t = slice, slice + 4,
+// ... in double-float, and the four partial sums meet in FP64.
+constexpr int UPD_SLICES = 4;
+__global__ void __launch_bounds__(256) kry_update(double2 *__restrict__ w, float4 *__restrict__ ws,
+                                                  const float4 *__restrict__ Q, int m,
                                                   const double2 *__restrict__ h, int64_t d) {
-  extern __shared__ double2 hs[];
-  for (int t = threadIdx.x; t < m; t += blockDim.x) hs[t] = h[t];
+  extern __shared__ float4 hs[];
+  __shared__ double2 part[UPD_SLICES][64];
+  for (int t = threadIdx.x; t < m; t += blockDim.x) hs[t] = df_split(h[t]);
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    double re = 0, im = 0;
-    for (int t = 0; t < m; ++t) {
-      const double2 q = Q[(int64_t)t * d + i];
-      const double2 c = hs[t];
-      re = fma(q.x, c.x, re);
-      re = fma(-q.y, c.y, re);
-      im = fma(q.x, c.y, im);
-      im = fma(q.y, c.x, im);
+  const int e = threadIdx.x & 63, slice = threadIdx.x >> 6;
+  for (int64_t i0 = (int64_t)blockIdx.x * 64; i0 < d; i0 += (int64_t)gridDim.x * 64) {
+    const int64_t i = i0 + e;
+    float rh = 0, rl = 0, ih = 0, il = 0;
+    if (i < d) {
+      for (int t = slice; t < m; t += UPD_SLICES) {
+        const float4 q = Q[(int64_t)t * d + i];
+        const float4 c = hs[t];  // q c
+        df_mac2(rh, rl, q.x, q.y, c.x, c.y);
+        df_mac2(rh, rl, -q.z, -q.w, c.z, c.w);
+        df_mac2(ih, il, q.x, q.y, c.z, c.w);
+        df_mac2(ih, il, q.z, q.w, c.x, c.y);
+      }
     }
-    double2 v = w[i];
-    v.x -= re;
-    v.y -= im;
-    w[i] = v;
+    part[slice][e] = make_double2((double)rh + (double)rl, (double)ih + (double)il);
+    __syncthreads();
+    if (slice == 0 && i < d) {
+      double re = 0, im = 0;
+#pragma unroll
+      for (int k = 0; k < UPD_SLICES; ++k) {
+        re += part[k][e].x;
+        im += part[k][e].y;
+      }
+      double2 v = w[i];
+      v.x -= re;
+      v.y -= im;
+      w[i] = v;
+      ws[i] = df_split(v);
+    }
+    __syncthreads();
   }
 }
 
@@ -207,7 +255,7 @@ __global__ void __launch_bounds__(RED_THREADS) kry_norm2(const double2 *__restri
 // scalars from device memory).  A vanishing beta (an invariant subspace) sets
 // *breakdown and leaves q_{j+1} = 0.
 __global__ void kry_close(const double2 *h1, const double2 *h2, int c, const double *nrm2, double tiny, double *alpha,
-                          double *beta, int j, const double2 *w, double2 *qn, int64_t d, int *breakdown) {
+                          double *beta, int j, const double2 *w, float4 *qn, int64_t d, int *breakdown) {
   const double b = sqrt(*nrm2);
   const bool dead = !(b > tiny);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -219,7 +267,7 @@ __global__ void kry_close(const double2 *h1, const double2 *h2, int c, const dou
   const double inv = dead ? 0.0 : 1.0 / b;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = w[i];
-    qn[i] = make_double2(v.x * inv, v.y * inv);
+    qn[i] = df_split(make_double2(v.x * inv, v.y * inv));  // the basis in split form
   }
 }
 
@@ -237,17 +285,18 @@ __global__ void kry_start(double2 *q, int64_t d, uint64_t seed) {
   }
 }
 
-__global__ void kry_scale(double2 *q, int64_t d, const double *nrm2) {
+// q (a basis row, split form) = v / ||v||
+__global__ void kry_scale(const double2 *v, float4 *q, int64_t d, const double *nrm2) {
   const double inv = 1.0 / sqrt(*nrm2);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = q[i];
-    q[i] = make_double2(v.x * inv, v.y * inv);
+    const double2 a = v[i];
+    q[i] = df_split(make_double2(a.x * inv, a.y * inv));
   }
 }
 
 // Ritz vectors: Z[:, k] = conj(sum_t S[t + k J] q_t) for k < m (Z column-major
 // d x m, S column-major J x m real); eight columns per thread.
-__global__ void __launch_bounds__(256) kry_ritz(const double2 *__restrict__ Q, int J, const double *__restrict__ S,
+__global__ void __launch_bounds__(256) kry_ritz(const float4 *__restrict__ Q, int J, const double *__restrict__ S,
                                                 int m, double2 *__restrict__ Z, int64_t d) {
   const int k0 = blockIdx.y * 8;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
@@ -255,7 +304,7 @@ __global__ void __launch_bounds__(256) kry_ritz(const double2 *__restrict__ Q, i
 #pragma unroll
     for (int k = 0; k < 8; ++k) re[k] = im[k] = 0.0;
     for (int t = 0; t < J; ++t) {
-      const double2 q = Q[(int64_t)t * d + i];
+      const double2 q = df_join(Q[(int64_t)t * d + i]);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         if (k0 + k < m) {
@@ -273,11 +322,11 @@ __global__ void __launch_bounds__(256) kry_ritz(const double2 *__restrict__ Q, i
 
 // Row-major copy of the conjugate Ritz vectors back into basis rows (for the
 // certification run): Q[t][i] = conj(Z[i + t d]).
-__global__ void kry_seed(const double2 *Z, int m, double2 *Q, int64_t d) {
+__global__ void kry_seed(const double2 *Z, int m, float4 *Q, int64_t d) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * d;
        e += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = Z[e];
-    Q[e] = make_double2(v.x, -v.y);
+    Q[e] = df_split(make_double2(v.x, -v.y));
   }
 }
 
@@ -330,9 +379,10 @@ __global__ void kry_eig_rho(const double *w_asc, int64_t r, double shift, double
 }
 
 struct KryBuffers {
-  double2 *M, *Q, *W, *h1, *h2, *Z;
+  double2 *M, *W, *h1, *h2, *Z;
+  float4 *Q;          // the Krylov basis, one row per vector, in split form (about 48 bits)
   const float2 *M32;  // the complex64 input, read by the double-float product
-  float4 *Xs;         // the current Lanczos vector split for it
+  float4 *Ws;         // the work vector W in split form
   double *alpha, *beta, *b2, *stats, *Wr, *Xr, *lu, *last, *nrm;
   int *cl, *nclust, *breakdown;
   SmolinResult *res;
@@ -411,24 +461,24 @@ lre_status lanczos_steps(lre_ctx *ctx, const KryBuffers &B, int64_t d, int64_t b
     const int64_t c = base + j;  // the row of q_j
     const int cols = (int)(c + 1);
     {
-      Launch L(ctx, "kry_matvec", s, 2);  // the split and the product
-      kry_split<<<(unsigned)((d + 255) / 256), 256, 0, s>>>(B.Q + c * d, B.Xs, d);
-      kry_matvec_df<MV_RPW><<<(unsigned)((d + 8 * MV_RPW - 1) / (8 * MV_RPW)), 256, 0, s>>>(B.M32, B.Xs, B.W, d);
+      Launch L(ctx, "kry_matvec", s);  // W = mu q_j and its split copy
+      kry_matvec_df<MV_RPW><<<(unsigned)((d + 8 * MV_RPW - 1) / (8 * MV_RPW)), 256, 0, s>>>(B.M32, B.Q + c * d, B.W,
+                                                                                          B.Ws, d);
     }
     {
       Launch L(ctx, "kry_reorth", s, 4);
       const int dg = (int)std::min<int64_t>(cols, 2048);
-      const size_t hs = (size_t)cols * sizeof(double2);
-      kry_dots<<<dg, RED_THREADS, 0, s>>>(B.Q, cols, B.W, B.h1, d);
-      kry_update<<<upd_grid, 64, hs, s>>>(B.W, B.Q, cols, B.h1, d);
-      kry_dots<<<dg, RED_THREADS, 0, s>>>(B.Q, cols, B.W, B.h2, d);
-      kry_update<<<upd_grid, 64, hs, s>>>(B.W, B.Q, cols, B.h2, d);
+      const size_t hs = (size_t)cols * sizeof(float4);
+      kry_dots<<<dg, RED_THREADS, 0, s>>>(B.Q, cols, B.Ws, B.h1, d);
+      kry_update<<<upd_grid, 256, hs, s>>>(B.W, B.Ws, B.Q, cols, B.h1, d);
+      kry_dots<<<dg, RED_THREADS, 0, s>>>(B.Q, cols, B.Ws, B.h2, d);
+      kry_update<<<upd_grid, 256, hs, s>>>(B.W, B.Ws, B.Q, cols, B.h2, d);
     }
     {
       Launch L(ctx, "kry_close", s, 2);
       cudaMemsetAsync(B.nrm, 0, sizeof(double), s);
       kry_norm2<<<red_grid, RED_THREADS, 0, s>>>(B.W, d, B.nrm);
-      double2 *next = c + 1 < B.rows ? B.Q + (c + 1) * d : nullptr;
+      float4 *next = c + 1 < B.rows ? B.Q + (c + 1) * d : nullptr;
       kry_close<<<red_grid, RED_THREADS, 0, s>>>(B.h1, B.h2, (int)c, B.nrm, tiny, alpha, beta, j, B.W, next, d,
                                                  B.breakdown);
     }
@@ -440,20 +490,21 @@ lre_status lanczos_steps(lre_ctx *ctx, const KryBuffers &B, int64_t d, int64_t b
 // A fresh unit start vector in row `row`, orthogonal to rows [0, row).
 lre_status start_vector(lre_ctx *ctx, const KryBuffers &B, int64_t d, int64_t row, uint64_t seed, cudaStream_t s) {
   const int red_grid = (int)std::min<int64_t>((d + RED_THREADS - 1) / RED_THREADS, (int64_t)ctx->num_sms * 4);
-  Launch L(ctx, "kry_start", s, 3);
-  double2 *q = B.Q + row * d;
-  kry_start<<<red_grid, RED_THREADS, 0, s>>>(q, d, seed);
+  // built in the FP64 work vector, stored into the basis row in split form
+  Launch L(ctx, "kry_start", s, row > 0 ? 8 : 3);
+  kry_start<<<red_grid, RED_THREADS, 0, s>>>(B.W, d, seed);
   if (row > 0) {
     const int cols = (int)row;
-    const size_t hs = (size_t)cols * sizeof(double2);
+    const size_t hs = (size_t)cols * sizeof(float4);
+    kry_split<<<red_grid, RED_THREADS, 0, s>>>(B.W, B.Ws, d);
     for (int pass = 0; pass < 2; ++pass) {
-      kry_dots<<<(int)std::min<int64_t>(cols, 2048), RED_THREADS, 0, s>>>(B.Q, cols, q, B.h1, d);
-      kry_update<<<(unsigned)((d + 63) / 64), 64, hs, s>>>(q, B.Q, cols, B.h1, d);
+      kry_dots<<<(int)std::min<int64_t>(cols, 2048), RED_THREADS, 0, s>>>(B.Q, cols, B.Ws, B.h1, d);
+      kry_update<<<(unsigned)((d + 63) / 64), 256, hs, s>>>(B.W, B.Ws, B.Q, cols, B.h1, d);
     }
   }
   cudaMemsetAsync(B.nrm, 0, sizeof(double), s);
-  kry_norm2<<<red_grid, RED_THREADS, 0, s>>>(q, d, B.nrm);
-  kry_scale<<<red_grid, RED_THREADS, 0, s>>>(q, d, B.nrm);
+  kry_norm2<<<red_grid, RED_THREADS, 0, s>>>(B.W, d, B.nrm);
+  kry_scale<<<red_grid, RED_THREADS, 0, s>>>(B.W, B.Q + row * d, d, B.nrm);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LRE_OK : cuda_fail(ctx, e, "Lanczos start vector");
 }
@@ -484,7 +535,7 @@ lre_status project_krylov(lre_ctx *ctx, cublasContext *blas, const lre_c64 *rho_
     return q;
   };
   B.M = reinterpret_cast<double2 *>(take((size_t)d * d * sizeof(double2)));
-  B.Q = reinterpret_cast<double2 *>(take((size_t)B.rows * d * sizeof(double2)));
+  B.Q = reinterpret_cast<float4 *>(take((size_t)B.rows * d * sizeof(float4)));
   B.W = reinterpret_cast<double2 *>(take((size_t)d * sizeof(double2)));
   B.h1 = reinterpret_cast<double2 *>(take((size_t)B.rows * sizeof(double2)));
   B.h2 = reinterpret_cast<double2 *>(take((size_t)B.rows * sizeof(double2)));
@@ -504,7 +555,7 @@ lre_status project_krylov(lre_ctx *ctx, cublasContext *blas, const lre_c64 *rho_
   B.res = reinterpret_cast<SmolinResult *>(take(sizeof(SmolinResult)));
   double *alpha2 = reinterpret_cast<double *>(take((size_t)KRY_VERIFY * sizeof(double)));
   double *beta2 = reinterpret_cast<double *>(take((size_t)KRY_VERIFY * sizeof(double)));
-  B.Xs = reinterpret_cast<float4 *>(take((size_t)d * sizeof(float4)));
+  B.Ws = reinterpret_cast<float4 *>(take((size_t)d * sizeof(float4)));
   B.M32 = reinterpret_cast<const float2 *>(rho_in);  // unchanged until the rebuild writes rho_out
 
   const int grid = ctx->num_sms * 8;
