@@ -137,8 +137,11 @@ lre_status lre_parity_sums(lre_ctx *ctx, const void *counts, lre_count_kind kind
  * lie in [0, shots_uniform]: the tensor-core first pass (lre_set_fold_path)
  * reads counts in a form where a larger value would change the result, so it
  * checks every count it reads and latches LRE_ERR_SHOTS_MISMATCH for one
- * outside that range (theta is then not defined); the FWHT path computes the
- * exact sums of whatever counts it is given. */
+ * outside that range (theta is then not defined); it also relies on every
+ * basis row summing to shots_uniform for the width of the partial sums it
+ * keeps, checks each partial against it, and latches the same error for a
+ * row whose partials exceed it.  The FWHT path computes the exact sums of
+ * whatever counts it is given. */
 lre_status lre_estimate(lre_ctx *ctx, const void *counts, lre_count_kind kind, const int64_t *shots,
                         int64_t shots_uniform, int n, double *theta, lre_c64 *rho,
                         lre_stream stream);
