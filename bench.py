@@ -165,6 +165,8 @@ KERNEL_SOURCES = {
                     "paper_1602_08604_gb300/csrc/sm103.cuh"],
     "fold_first6_mma": ["paper_1602_08604_gb300/csrc/fold_mma.cu", "paper_1602_08604_gb300/csrc/passes.cuh",
                         "paper_1602_08604_gb300/csrc/sm103.cuh"],
+    "fold_first7_mma": ["paper_1602_08604_gb300/csrc/fold_mma.cu", "paper_1602_08604_gb300/csrc/passes.cuh",
+                        "paper_1602_08604_gb300/csrc/sm103.cuh"],
 }
 
 
@@ -315,7 +317,7 @@ def run_e2e(args, wl, lre, torch, device, theta_dev):
 
 
 FIRST_PASS_KERNELS = ("fold_first6", "fold_first6_mma", "fold_first6_mma_split", "fold_first9_fused",
-                      "fold_first6_mma_records", "fold_first9_mma")
+                      "fold_first6_mma_records", "fold_first9_mma", "fold_first7_mma")
 
 
 def timed_steps(lre, ctx, torch, stream, step, steps, warmup):
@@ -391,16 +393,30 @@ def set_first_variant(lre, ctx, variant, consumers=0, discard=0):
         raise RuntimeError("fused-pass consumer count rejected")
 
 
+def set_first7(lre, ctx, on):
+    """Test hook: the raw tensor-core first pass folds seven qubits where it
+    applies (1) or six (0, the library default)."""
+    import ctypes
+    f = lre.load().lre_debug_set_first7
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_int
+    if f(ctx, int(on)) != 0:
+        raise RuntimeError("first7 setting rejected")
+
+
 def arm_record(lre, torch, device, stream, counts, wl, workload, path, steps, warmup, theta_ref=None,
-               first_variant=None, consumers=0, discard=0):
+               first_variant=None, consumers=0, discard=0, first7=None):
     """One timed arm of lre_estimate on resident counts with the first fold
     pass on the tensor cores or on the ALUs (FWHT), in a context of its own;
-    first_variant 2: the first pass fused with the second through L2."""
+    first_variant 2: the first pass fused with the second through L2;
+    first7 1: the raw tensor-core first pass folds seven qubits, not six."""
     n = wl["n"]
     ctx = lre.lre_create(device.index)
     try:
         if first_variant is not None:
             set_first_variant(lre, ctx, first_variant, consumers, discard)
+        if first7 is not None:
+            set_first7(lre, ctx, first7)
         lre.lre_set_fold_path(ctx, {"tensor": lre.LRE_FOLD_TENSOR, "tensor_split": lre.LRE_FOLD_TENSOR_SPLIT,
                                     "fwht": lre.LRE_FOLD_FWHT}[path])
         theta = torch.empty(4 ** n, dtype=torch.float64, device=device)
@@ -497,6 +513,8 @@ def run_ours(args, wl):
                                 "fwht": lre.LRE_FOLD_FWHT}[args.fold_path])
     if args.fused_first:
         set_first_variant(lre, ctx, 2, args.fused_consumers, args.fused_discard)
+    if args.first7:
+        set_first7(lre, ctx, 1)
     stream = torch.cuda.current_stream(device)
 
     def step():
@@ -530,6 +548,12 @@ def run_ours(args, wl):
         compare[f"{args.workload}_{other}"], _ = arm_record(
             lre, torch, device, stream, counts, wl, args.workload, other, args.compare_steps, 2, theta_ref=theta)
         torch.cuda.empty_cache()
+        if args.fold_path == "tensor" and not args.fused_first and not args.first7 and n >= 8:
+            # the tensor-core first pass folding seven qubits (then one later pass fewer)
+            compare[f"{args.workload}_first_pass_seven_qubits"], _ = arm_record(
+                lre, torch, device, stream, counts, wl, args.workload, "tensor", args.compare_steps, 2,
+                theta_ref=theta, first7=1)
+            torch.cuda.empty_cache()
         if args.fold_path == "tensor" and not args.fused_first:
             # the first pass fused with the second through an L2 ring
             compare[f"{args.workload}_fused_first_second"], _ = arm_record(
@@ -890,6 +914,8 @@ def main():
     ap.add_argument("--fold-path", default="tensor", choices=["fwht", "tensor", "tensor_split"],
                     help="first fold pass on the tensor cores (the library default: int16 counts), also for "
                          "int32 counts as two fp16 planes (tensor_split), or on the ALUs (FWHT)")
+    ap.add_argument("--first7", action="store_true",
+                    help="the raw tensor-core first pass folds seven qubits instead of six")
     ap.add_argument("--fused-first", action="store_true",
                     help="the first fold pass fused with the second through an L2 ring (n >= 10)")
     ap.add_argument("--fused-consumers", type=int, default=0,

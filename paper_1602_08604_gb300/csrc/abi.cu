@@ -431,6 +431,15 @@ extern "C" lre_status lre_debug_set_fused_consumers(lre_ctx *ctx, int ctas, int 
   return LRE_OK;
 }
 
+// Test hook (not part of include/lre.h): 1 lets the raw tensor-core first
+// pass of a whole fold (not a streamed one) fold seven qubits where it
+// applies (n >= 8); 0 (the default) keeps it at six.
+extern "C" lre_status lre_debug_set_first7(lre_ctx *ctx, int on) {
+  if (!ctx || on < 0 || on > 1) return LRE_ERR_INVALID_ARG;
+  ctx->first7 = on;
+  return LRE_OK;
+}
+
 // Test hook (not part of include/lre.h): CTAs of the tensor-core first pass
 // (0: one per SM, the default; fewer leave SMs idle, to measure how its rate
 // grows with the SMs that run it).

@@ -551,7 +551,7 @@ GenKernel pick_generic(int J, int in_t, int acc_t, int mode, bool weight) {
 int type_size(int t) { return t == T_I16 ? 2 : (t == T_I32 ? 4 : 8); }
 
 struct PassPlan {
-  bool first6;
+  bool first6;  // a tiled first pass: six qubits (J = 6), or seven (J = 7, the raw tensor-core pass)
   bool fused9;  // first pass fused with the second through L2 (6 + 3 qubits)
   int J, r, in_t, acc_t, mode;
   bool weight;
@@ -560,9 +560,10 @@ struct PassPlan {
 };
 
 // Build the pass schedule.  shots_bound: an upper bound on every basis' total
-// count (decides int32 vs int64 partial sums); weighted: FP64 path.
+// count (decides int32 vs int64 partial sums); weighted: FP64 path; first7:
+// the caller runs the raw tensor-core first pass, which may fold seven qubits.
 std::vector<PassPlan> make_plan(int n, lre_count_kind kind, bool weighted, bool parity,
-                                int64_t shots_bound, bool aligned16, int variant) {
+                                int64_t shots_bound, bool aligned16, int variant, bool first7 = false) {
   std::vector<PassPlan> plan;
   int r = n, t = 0;
   int64_t C = 1;
@@ -585,6 +586,21 @@ std::vector<PassPlan> make_plan(int n, lre_count_kind kind, bool weighted, bool 
     r -= 9;
     t += 9;
     C <<= 18;
+    in_t = T_I32;
+  } else if (first7 && !weighted && kind == LRE_COUNTS_I16 && r > 7 && aligned16 && fits32(7)) {
+    PassPlan p{};
+    p.first6 = true;
+    p.J = 7;
+    p.r = r;
+    p.in_t = in_t;
+    p.acc_t = T_I32;
+    p.mode = M_STORE;
+    p.C = C;
+    p.out_bytes = (size_t)ipow(6, r - 7) * 16384 * 4;
+    plan.push_back(p);
+    r -= 7;
+    t += 7;
+    C *= 16384;
     in_t = T_I32;
   } else if (!weighted && n >= 6 && r > 6 && aligned16 && fits32(6)) {
     PassPlan p{};
@@ -678,11 +694,16 @@ size_t fuse_bytes(const std::vector<PassPlan> &plan) {
 }
 
 size_t fold_workspace_bytes(int n, lre_count_kind kind, bool weighted, int64_t shots_bound, int variant) {
-  auto plan = make_plan(n, kind, weighted, false, shots_bound, true, variant);
-  size_t a, b;
-  plan_buffers(plan, a, b);
-  size_t w = weighted ? round_up((size_t)ipow(3, n) * sizeof(double)) : 0;
-  return round_up(a) + round_up(b) + w + fuse_bytes(plan);
+  size_t most = 0;
+  for (int seven = 0; seven < 2; ++seven) {  // room for either first pass
+    auto plan = make_plan(n, kind, weighted, false, shots_bound, true, variant, seven != 0);
+    size_t a, b;
+    plan_buffers(plan, a, b);
+    size_t w = weighted ? round_up((size_t)ipow(3, n) * sizeof(double)) : 0;
+    const size_t need = round_up(a) + round_up(b) + w + fuse_bytes(plan);
+    if (need > most) most = need;
+  }
+  return most;
 }
 
 __global__ void inv_shots_kernel(const int64_t *shots, double *w, int64_t B, int *status) {
@@ -701,8 +722,9 @@ namespace {
 int tensor_variant(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
   if (!pp.first6 || ctx->fold_path < 1 || !ctx->mma_operand || a.shots != nullptr || a.shots_uniform <= 0)
     return -1;
-  const int v = pp.in_t == T_I16 ? ctx->mma_biased : (pp.in_t == T_I32 && ctx->fold_path == 2 ? 3 : -1);
+  int v = pp.in_t == T_I16 ? ctx->mma_biased : (pp.in_t == T_I32 && ctx->fold_path == 2 ? 3 : -1);
   if (pp.fused9 && v != 0) return -1;  // the fused first + second pass exists for the raw encoding
+  if (pp.J == 7) v = v == 0 ? MMA_SEVEN : -1;  // and the seven-qubit pass
   return v >= 0 && a.shots_uniform <= mma_max_count(v) ? v : -1;
 }
 
@@ -715,8 +737,23 @@ bool tensor_first_pass(lre_ctx *ctx, const PassPlan &pp, const FoldArgs &a) {
 // pass is a TMA-staged store pass that reads them back.
 bool use_planes(lre_ctx *ctx, const std::vector<PassPlan> &plan, const FoldArgs &a) {
   return !plan.empty() && !plan[0].fused9 && tensor_first_pass(ctx, plan[0], a) && plan.size() > 1 &&
-         a.shots_uniform * 729 < (1ll << 23) && plan[1].mode == M_STORE && plan[1].in_t == T_I32 &&
-         ctx->generic_tma && plan[1].C % 32 == 0;
+         a.shots_uniform * (plan[0].J == 7 ? 2187 : 729) < (1ll << 23) && plan[1].mode == M_STORE &&
+         plan[1].in_t == T_I32 && ctx->generic_tma && plan[1].C % 32 == 0;
+}
+
+// The schedule of a fold: the seven-qubit first pass where the raw
+// tensor-core pass runs over a whole fold (stage 0, counts in memory),
+// otherwise the six-qubit one (streamed folds always: their chunks are tile
+// rows of the six-qubit pass).
+std::vector<PassPlan> fold_plan(lre_ctx *ctx, const FoldArgs &a, bool weighted, bool parity, int64_t bound,
+                                bool aligned16) {
+  auto plan = make_plan(a.n, a.kind, weighted, parity, bound, aligned16, ctx->first_variant);
+  if (ctx->first7 && a.stage == 0 && !a.rec_entries && !plan.empty() && plan[0].first6 && !plan[0].fused9 &&
+      tensor_variant(ctx, plan[0], a) == 0) {
+    auto p7 = make_plan(a.n, a.kind, weighted, parity, bound, aligned16, ctx->first_variant, true);
+    if (!p7.empty() && p7[0].J == 7 && tensor_variant(ctx, p7[0], a) == MMA_SEVEN) return p7;
+  }
+  return plan;
 }
 
 }  // namespace
@@ -751,7 +788,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
   const bool parity = a.S != nullptr;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(a.counts) & 15) == 0;
   const int64_t bound = weighted ? 0 : a.shots_uniform;
-  auto plan = make_plan(a.n, a.kind, weighted, parity, bound, aligned16, ctx->first_variant);
+  auto plan = fold_plan(ctx, a, weighted, parity, bound, aligned16);
   size_t bA, bB;
   plan_buffers(plan, bA, bB);
   char *p = static_cast<char *>(ws);
@@ -822,7 +859,7 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
         ctx->last_error = "tensor map of the counts rejected";
         return LRE_ERR_CUDA;
       }
-      const int64_t elems = ipow(6, pp.r - 6) * 4096;
+      const int64_t elems = pp.J == 7 ? ipow(6, pp.r - 7) * 16384 : ipow(6, pp.r - 6) * 4096;
       int8_t *hi = planes ? static_cast<int8_t *>(out) + elems * 2 : nullptr;
       lre_status st = mma_first_pass(ctx, tmap, tmap_tail, ctx->mma_operand, static_cast<int32_t *>(out), hi,
                                      pp.r, tensor_variant(ctx, pp, a), a.shots_uniform, tile_begin, tile_end,
@@ -900,6 +937,8 @@ lre_status fold_run(lre_ctx *ctx, const FoldArgs &a, void *ws, size_t ws_bytes, 
       }
       gp.status = ctx->d_status;
       gp.hi_from = planes_hi_from(a.shots_uniform);
+      gp.hi_letters = plan[0].J == 7 ? 7 : 6;
+      gp.top7 = plan[0].J == 7 ? 1 : 0;  // the seven-qubit first pass folded qubit n
       const int in_t = (planes && k == 1) ? (int)T_I24P : pp.in_t;
       lre_status tst = ctx->generic_tma ? tma_pass(ctx, gp, pp.J, in_t, pp.acc_t, pp.mode, pp.weight, s)
                                         : LRE_ERR_UNSUPPORTED;
@@ -938,13 +977,15 @@ __global__ void debug_div_kernel(const int64_t *S, int64_t count, int64_t D, dou
 // Test hook (not part of include/lre.h; host only, no device work): the
 // fold pass schedule for these arguments.  Per pass, 9 int64 at out + 9 k:
 // first6, fused9, J, r, in_t, acc_t, mode, C, out_bytes (at most max_passes
-// written).  Returns the number of passes, or -1 for n outside 1..14.
+// written).  variant: the first-pass variant (0..2), plus 256 when the raw
+// tensor-core first pass runs (the seven-qubit pass may be planned).
+// Returns the number of passes, or -1 for n outside 1..14.
 extern "C" int lre_debug_fold_plan(int n, int kind, int weighted, int parity, int64_t shots_bound, int aligned16,
                                    int variant, int64_t *out, int max_passes) {
   using namespace lre;
   if (n < 1 || n > 14) return -1;
   const auto plan = make_plan(n, static_cast<lre_count_kind>(kind), weighted != 0, parity != 0, shots_bound,
-                              aligned16 != 0, variant);
+                              aligned16 != 0, variant & 255, (variant & 256) != 0);
   for (int k = 0; out && k < (int)plan.size() && k < max_passes; ++k) {
     const PassPlan &p = plan[k];
     const int64_t v[9] = {p.first6, p.fused9, p.J, p.r, p.in_t, p.acc_t, p.mode, p.C, (int64_t)p.out_bytes};

@@ -79,7 +79,30 @@ namespace {
 
 using namespace passes;
 
-enum : int { V_RAW = 0, V_BIASED = 1, V_RECORDS = 2, V_SPLIT = 3, V_RAW9 = 4 };
+enum : int { V_RAW = 0, V_BIASED = 1, V_RECORDS = 2, V_SPLIT = 3, V_RAW9 = 4, V_RAW7 = MMA_SEVEN };
+
+// V_RAW7: the raw pass folding seven qubits: the six of the tile and the
+// last one, qubit n (the top ternary digit of ah, the top bit of oh), so
+// that CTAs working side by side still read neighbouring 128-byte count
+// chunks (qubit 7, whose outcome is bit 0 of oh, would have them read every
+// other chunk at a time: 256-byte L2 lines fetched twice as fast as used).
+// Tiles come in groups of six, a supertile (AH, OH): the three axes a times
+// the two outcomes o of qubit n, ah = AH + a 3^(n-7), oh = OH + o 2^(n-7), in
+// the order (a, o) = (0,0), (0,1), (1,0), ... .  Every tile's level A and B
+// run as in the six-qubit pass; then the level-B warps of lanes 0..63 (pair
+// 0) add all six results into the letter I of qubit n, and those of lanes
+// 64..127 (pair 1, the same values, since rows 64..127 of the operand repeat
+// Tt) take D(a, 0) - D(a, 1) into the letter a + 1 (the outcome-1 tile
+// converted with the opposite sign).  Both pairs read every tile, from the
+// two TMEM tile buffers in turn.  The output is [3^(n-7)][2^(n-7)][16384],
+// column pn * 4096 + plB * 64 + plA: four blocks where the six-qubit pass
+// writes six, and the later passes (qubits 7..n-1) have one qubit less to
+// fold; the final pass puts qubit n's letter back at the top of the index.
+// Measured at n = 14 (1000 shots): the later passes drop from 5.4 to 4.2 ms,
+// but this pass takes 28.3 ms against the six-qubit pass's 25.6-25.9: its
+// CTAs end between 24.6 and 27.9 ms where the six-qubit pass's end within
+// 0.2 ms (dealing supertiles out dynamically made it 30.4 ms), so the six
+// qubit pass stays the default (lre_debug_set_first7 selects this one).
 
 // V_RAW9: the raw pass fused with the second fold pass (three more qubits)
 // through L2, in one cooperative launch whose CTAs take one of two roles.
@@ -167,7 +190,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
                     const int32_t *__restrict__ offs, int64_t shots, int64_t row_base, int32_t *__restrict__ scratch,
                     unsigned *__restrict__ f9, int *status) {
   constexpr bool BIASED = V == V_BIASED, RECORDS = V == V_RECORDS, SPLIT = V == V_SPLIT;
-  constexpr bool RAWLIKE = V == V_RAW || V == V_RAW9, F9 = V == V_RAW9;
+  constexpr bool RAWLIKE = V == V_RAW || V == V_RAW9 || V == V_RAW7, F9 = V == V_RAW9, SEVEN = V == V_RAW7;
   // F9 counters: f9[0] the next job, f9[1 + s] tiles done, f9[1 + F9_RING + s] jobs done (slot s)
   constexpr int CPT = MmaCfg<V>::CPT;
   constexpr int MR = MmaCfg<V>::R;          // ring slots
@@ -202,7 +225,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       sm103::mbar_init(&tile_done[b], 1);
-      sm103::mbar_init(&tile_free[b], 64);
+      sm103::mbar_init(&tile_free[b], SEVEN ? 128 : 64);  // SEVEN: both pairs read every tile
     }
     sm103::fence_barrier_init();
   }
@@ -217,9 +240,19 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     latch(status, LRE_ERR_TIMEOUT);
   };
   const int64_t tiles = tile_end - tile_begin;
-  const int64_t my_tiles = (!consumer && tiles > blockIdx.x) ? (tiles - blockIdx.x + nP - 1) / nP : 0;
+  // units of work dealt out over the CTAs in turn: tiles, or SEVEN supertiles of six
+  const int64_t units = SEVEN ? tiles / 6 : tiles;
+  const int64_t my_units = (!consumer && units > blockIdx.x) ? (units - blockIdx.x + nP - 1) / nP : 0;
+  const int64_t my_tiles = SEVEN ? 6 * my_units : my_units;
   const int64_t total = my_tiles * CPT;  // chunks of this CTA
-  const bool conv_warp = SPLIT ? (warp == 2 || warp == 3 || warp == 8 || warp == 9) : (warp == 2 || warp == 3);
+  // SEVEN: the level-B work of every tile is done twice (both pairs), so it
+  // is kept off warp 1's sub-partition (warp % 4 == 1, whose MMA issue sets
+  // the pace): level B on warps 4, 6 (TMEM lanes 0..31 / 64..95) and 3, 7
+  // (lanes 96..127), the range check on warps 2 and 5
+  const bool conv_warp = SPLIT   ? (warp == 2 || warp == 3 || warp == 8 || warp == 9)
+                         : SEVEN ? (warp == 2 || warp == 5)
+                                 : (warp == 2 || warp == 3);
+  const bool levelb_warp = SEVEN ? (warp == 3 || warp == 4 || warp == 6 || warp == 7) : (warp >= 4 && warp < 8);
 
   if (consumer) {
     // second pass (qubits 7..9): warp cw takes jobs cw, cw + W, ...; a job is
@@ -376,6 +409,12 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
           const int64_t gah = G / n_goh, goh = G - gah * n_goh;
           ah = gah * 27 + k / 8;
           oh = goh * 8 + (k & 7);
+        } else if constexpr (SEVEN) {  // supertile st = (AH, OH), tile t6 = (a, o) of qubit n
+          const int64_t lt = g / CPT, st = blockIdx.x + (lt / 6) * nP, n_oh2 = n_oh >> 1;
+          const int t6 = (int)(lt % 6);
+          const int64_t AH = st / n_oh2, OH = st - AH * n_oh2;
+          ah = AH + (t6 >> 1) * (units / n_oh2);  // units / 2^(n-7) = 3^(n-7)
+          oh = OH + (t6 & 1) * n_oh2;
         } else {
           ah = tile / n_oh;
           oh = tile - ah * n_oh;
@@ -511,7 +550,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         const int rows = c ? (int)(BOX_BIG + BOX_TAIL) : (int)(2 * BOX_BIG);
         uint4 *v4 = reinterpret_cast<uint4 *>(base);
 #pragma unroll 4
-        for (int k = (warp - 2) * 32 + lane; k < rows * 8; k += 64) {
+        for (int k = (SEVEN ? (warp == 5) : warp - 2) * 32 + lane; k < rows * 8; k += 64) {
           uint4 v = v4[k];
           mx = __vmaxu2(__vmaxu2(mx, v.x), __vmaxu2(v.y, __vmaxu2(v.z, v.w)));
           if constexpr (BIASED) {  // counts -> fp16(1024 + c)
@@ -533,9 +572,10 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
     const uint32_t top = SPLIT ? mx : max(mx & 0xFFFFu, mx >> 16);
     const int64_t lim = BIASED ? (shots < 1023 ? shots : 1023) : shots;
     if ((int64_t)top > lim) latch(status, LRE_ERR_SHOTS_MISMATCH);
-  } else if (warp >= 4 && warp < 8) {
+  } else if (levelb_warp) {
     // warps 4,5: even tiles, TMEM lanes 0..63; warps 6,7: odd tiles, lanes 64..127
-    const int pair = (warp - 4) >> 1;
+    // (SEVEN: pair 0 = warps 4, 3 and pair 1 = warps 6, 7, every tile)
+    const int pair = SEVEN ? (warp == 6 || warp == 7) : (warp - 4) >> 1;
     const int quarter = warp & 3;
     const int plA = (quarter & 1) * 32 + lane;
     const int hi_from = planes_hi_from(shots);  // split planes: identities from which the high plane counts
@@ -550,16 +590,27 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
       __syncwarp();
       if (lane == 0) atomicAdd(f9 + 1 + slot, 1u);
     };
-    for (int64_t lt = pair; lt < my_tiles; lt += 2) {
-      if (!sm103::mbar_wait(&tile_done[pair], (uint32_t)((lt >> 1) & 1), abort_flag)) {
+    int32_t acc[64];  // SEVEN: carried over the tiles one output block gathers
+    // SEVEN: both pairs take every tile, from the buffers in turn; otherwise
+    // pair b takes the tiles of buffer b
+    for (int64_t lt = SEVEN ? 0 : pair; lt < my_tiles; lt += SEVEN ? 1 : 2) {
+      const int tb = SEVEN ? (int)(lt & 1) : pair;
+      if (!sm103::mbar_wait(&tile_done[tb], (uint32_t)((lt >> 1) & 1), abort_flag)) {
         give_up();
         break;
       }
       sm103::tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + pair * TILE_COLS;
-      int32_t acc[64];
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + tb * TILE_COLS;
+      // SEVEN: tile t6 = (a, o) of its supertile; pair 0 gathers all six
+      // (letter I), pair 1 the two of one axis, the o = 1 tile negated
+      const int t6 = SEVEN ? (int)(lt % 6) : 0;
+      const bool fresh = !SEVEN || (pair == 0 ? t6 == 0 : (t6 & 1) == 0);
+      const bool flush = !SEVEN || (pair == 0 ? t6 == 5 : (t6 & 1) == 1);
+      const float sc = (SEVEN && pair == 1 && (t6 & 1)) ? -scale : scale;
+      if (fresh) {
 #pragma unroll
-      for (int p = 0; p < 64; ++p) acc[p] = 0;
+        for (int p = 0; p < 64; ++p) acc[p] = 0;
+      }
       // columns 32 grp .. 32 grp + 31 hold alB = 4 grp .. 4 grp + 3; the load of
       // the next 32 columns is in flight while these are contracted
       uint32_t r[2][32];
@@ -574,7 +625,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
           if (alB < 27) {
             int32_t v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = d_to_int(r[grp & 1][j * 8 + i], scale, sub);
+            for (int i = 0; i < 8; ++i) v[i] = d_to_int(r[grp & 1][j * 8 + i], sc, sub);
             wht<3>(v);
 #pragma unroll
             for (int m = 0; m < 8; ++m) acc[block_pauli(alB, m, 3)] += v[m];
@@ -582,8 +633,14 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         }
       }
       sm103::tc_fence_before();
-      sm103::mbar_arrive(&tile_free[pair]);
+      sm103::mbar_arrive(&tile_free[tb]);
+      if (!flush) continue;
       const int64_t tile = tile_begin + blockIdx.x + lt * nP;
+      // first element of this output block, and its column within the row
+      // of letters (the split planes' run bound depends on it)
+      const int blk = pair == 0 ? 0 : (t6 >> 1) + 1;
+      const int64_t row = SEVEN ? ((int64_t)blockIdx.x + (lt / 6) * nP) * 16384 + blk * 4096 : tile * 4096;
+      const int col = SEVEN ? blk * 4096 : 0;
       if constexpr (F9) {
         // the previous tile's stores have had this tile's work to complete:
         // count it now, so that its fence does not wait on them
@@ -603,13 +660,13 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         for (int p = 0; p < 64; ++p) o[p * 64] = acc[p];  // stays in L2 for the second pass
         pend = slot;
       } else if (out_hi) {  // split planes: low 16 bits, then the (signed) bits above
-        unsigned short *lo = reinterpret_cast<unsigned short *>(out) + tile * 4096 + plA;
-        signed char *hi = reinterpret_cast<signed char *>(out_hi) + tile * 4096 + plA;
+        unsigned short *lo = reinterpret_cast<unsigned short *>(out) + row + plA;
+        signed char *hi = reinterpret_cast<signed char *>(out_hi) + row + plA;
         bool bad = false;  // a partial the planes cannot hold: a row above its shots
 #pragma unroll
         for (int p = 0; p < 64; ++p) {
           __stcs(lo + p * 64, (unsigned short)(acc[p] & 0xFFFF));
-          if (planes_hi_needed((int64_t)p * 64 + (quarter & 1) * 32, hi_from)) {  // warp-uniform
+          if (planes_hi_needed(col + p * 64 + (quarter & 1) * 32, hi_from, SEVEN ? 7 : 6)) {  // warp-uniform
             __stcs(hi + p * 64, (signed char)(acc[p] >> 16));
             bad |= acc[p] >= (1 << 23) || acc[p] < -(1 << 23);
           } else {
@@ -618,7 +675,7 @@ __global__ void __launch_bounds__(MmaCfg<V>::THREADS, 1)
         }
         if (bad) latch(status, LRE_ERR_SHOTS_MISMATCH);
       } else {
-        int32_t *o = out + tile * 4096 + plA;
+        int32_t *o = out + row + plA;
 #pragma unroll
         for (int p = 0; p < 64; ++p) __stcs(o + p * 64, acc[p]);
       }
@@ -672,10 +729,12 @@ int64_t mma_max_count(int variant) { return variant == 1 ? 1023 : (variant == 3 
 
 // Launch the tensor-core first pass over tiles [tile_begin, tile_end) of an
 // n-qubit count matrix (tile = ah * 2^(n-6) + oh): variant 0 (RAW) or 1
-// (BIASED) for int16 counts, 3 (SPLIT) for int32 counts.  out_hi == nullptr:
-// int32 partials at out; otherwise split planes, the low 16 bits at out (as
-// uint16) and the bits above at out_hi (int8), exact while every partial is
-// below 2^23 in magnitude (729 x shots).  map_big / map_tail are tensor maps
+// (BIASED) for int16 counts, 3 (SPLIT) for int32 counts; variant 5 (RAW,
+// seven qubits folded, n >= 8) over all tiles only, output
+// [3^(n-7)][2^(n-7)][16384].  out_hi == nullptr: int32 partials at out;
+// otherwise split planes, the low 16 bits at out (as uint16) and the bits
+// above at out_hi (int8), exact while every partial is below 2^23 in
+// magnitude (729 x shots, 2187 x shots for variant 5).  map_big / map_tail are tensor maps
 // of the counts (int16, or int32 for SPLIT) with boxes of 216 / 81 rows x 64
 // outcomes, whose row 0 is basis row_base; a_dev holds the operand written by
 // mma_operand_upload; shots is the shots per basis, at most
@@ -685,13 +744,19 @@ lre_status mma_first_pass(lre_ctx *ctx, const CUtensorMap &map_big, const CUtens
                           int64_t tile_end, int64_t row_base, cudaStream_t s) {
   const int64_t tiles = tile_end - tile_begin;
   if (tiles <= 0) return LRE_OK;
-  if (shots <= 0 || shots > mma_max_count(variant) || (variant != 0 && variant != 1 && variant != 3))
+  if (shots <= 0 || shots > mma_max_count(variant) ||
+      (variant != 0 && variant != 1 && variant != 3 && variant != V_RAW7))
     return LRE_ERR_UNSUPPORTED;
+  const bool seven = variant == V_RAW7;
+  if (seven && (n < 8 || tile_begin != 0 || row_base != 0 || tiles != (ipow(3, n - 6) << (n - 6))))
+    return LRE_ERR_UNSUPPORTED;
+  const int64_t units = seven ? tiles / 6 : tiles;
   const int ctas = ctx->first_grid > 0 ? ctx->first_grid : ctx->num_sms;
-  const int grid = (int)(tiles < ctas ? tiles : ctas);
-  Launch L(ctx, variant == 3 ? "fold_first6_mma_split" : "fold_first6_mma", s);
+  const int grid = (int)(units < ctas ? units : ctas);
+  Launch L(ctx, variant == 3 ? "fold_first6_mma_split" : (seven ? "fold_first7_mma" : "fold_first6_mma"), s);
   auto kern = variant == 3 ? fold_first6_mma<V_SPLIT>
-                           : (variant == 1 ? fold_first6_mma<V_BIASED> : fold_first6_mma<V_RAW>);
+                           : (variant == 1 ? fold_first6_mma<V_BIASED>
+                                           : (seven ? fold_first6_mma<V_RAW7> : fold_first6_mma<V_RAW>));
   const int threads = variant == 3 ? MmaCfg<V_SPLIT>::THREADS : MMA_THREADS;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MMA_SMEM);
   kern<<<grid, threads, MMA_SMEM, s>>>(map_big, map_tail, map_tail, grid, 0, static_cast<const uint4 *>(a_dev), out,

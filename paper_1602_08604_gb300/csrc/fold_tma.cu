@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(tma_warps<J>() * 32, 1) fold_tma(const __grid_
   // in step and share the 256-byte L2 lines of both planes), but the high
   // plane holds values only where one of a task's letters can need it; the
   // others take the low 16 bits as int16
-  auto with_hi = [&](int64_t task) { return PLANES && planes_hi_needed((task % cblocks) * TC, P.hi_from); };
+  auto with_hi = [&](int64_t task) {
+    return PLANES && planes_hi_needed((task % cblocks) * TC, P.hi_from, P.hi_letters);
+  };
   auto issue = [&](int64_t task, int b) {
     const int64_t ahoh = task / cblocks, cb = task - ahoh * cblocks;
     const int64_t ah = ahoh / P.n_oh, oh = ahoh - ah * P.n_oh;

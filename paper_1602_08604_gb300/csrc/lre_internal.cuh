@@ -52,6 +52,7 @@ struct lre_ctx {
   int fused_consumers = 0;    // tensor-core fused pass: CTAs on the second pass (0: a sixth of the SMs)
   int fused_discard = 0;      // tensor-core fused pass: 1 = drop consumed ring lines from L2
   int first_grid = 0;         // tensor-core first pass: CTAs (0: one per SM)
+  int first7 = 0;             // tensor-core raw first pass: 1 = fold seven qubits where it applies
   int fold_path = 1;          // first pass: 0 FWHT on the ALU, 1 tensor cores for int16 counts, 2 also int32
   void *mma_operand = nullptr;  // device copy of the constant tensor-core operand
   int mma_biased = 0;         // tensor-core operand: 0 raw counts as fp16 bits, 1 fp16(1024 + c)
@@ -217,8 +218,10 @@ size_t mma_operand_bytes();
 // 1 the tail (81 rows)
 uint32_t mma_box_rows(int which, int variant);
 // largest count the operand encoding keeps exact: variant 0 raw int16 (2047),
-// 1 biased int16 (1023), 3 int32 in two planes (16383)
+// 1 biased int16 (1023), 3 int32 in two planes (16383), MMA_SEVEN raw int16
 int64_t mma_max_count(int variant);
+// variant of mma_first_pass that folds seven qubits (the raw encoding)
+constexpr int MMA_SEVEN = 5;
 lre_status mma_operand_upload(lre_ctx *ctx, void *a_dev, cudaStream_t s);
 // the raw tensor-core pass fused with the second fold pass through an L2 ring
 lre_status mma_first_pass_fused9(lre_ctx *ctx, const CUtensorMap &map_big, const CUtensorMap &map_tail,

@@ -142,28 +142,32 @@ struct GenParams {
   int64_t dint[16];      // N 3^k as an integer (uniform shots)
   double recip[16];      // correctly rounded 1 / denom[k]
   int64_t up3[16];       // 3^(n-k)
-  int hi_from;           // split-plane input: see planes_hi_needed
+  int hi_from = 0;       // split-plane input: see planes_hi_needed
+  int hi_letters = 6;    // split-plane input: qubits the first pass folded (6 or 7)
+  int top7 = 0;          // last pass: letter 6 of the columns is qubit n's (seven-qubit first pass)
 };
 
 // Split-plane partials of the tensor-core first pass: the partial of a letter
-// with k identities among its six qubits is at most shots 3^k in magnitude
-// (each basis row sums to the shots), so its high plane (bits 16..23) is
-// needed only from k = hi_from on, the least k with shots 3^k > 32767; below
-// that the low 16 bits, read as int16, are the value.  Letters are numbered
-// plB * 64 + plA (three letters each, 2 bits a letter, 0 = I) and a run of 32
-// from c0 (a multiple of 32) fixes plB and the top bit of plA's third
-// letter: its most identities are those of plB plus 3 (lower half, that
-// letter I or X) or 2 (upper half, Y or Z).  The high plane of such a run is
+// with k identities among its six (or seven) qubits is at most shots 3^k in
+// magnitude (each basis row sums to the shots), so its high plane (bits
+// 16..23) is needed only from k = hi_from on, the least k with shots 3^k >
+// 32767; below that the low 16 bits, read as int16, are the value.  Letters
+// are numbered (p7 * 64 +) plB * 64 + plA (2 bits a qubit, 0 = I; p7 only
+// for the seven-qubit pass) and a run of 32 from c0 (a multiple of 32) fixes
+// every letter above plA and the top bit of plA's third letter: its most
+// identities are those of the fixed letters plus 3 (lower half, that letter
+// I or X) or 2 (upper half, Y or Z).  The high plane of such a run is
 // written only when one of its letters can need it, and read as values only
 // then (the reader loads every run's bytes: whole L2 lines stream faster).
 __host__ __device__ inline int planes_hi_from(int64_t shots) {
   int k = 0;
-  for (int64_t b = shots; k < 7 && b <= 32767; ++k) b *= 3;
+  for (int64_t b = shots; k < 8 && b <= 32767; ++k) b *= 3;
   return k;
 }
-__host__ __device__ inline bool planes_hi_needed(int64_t c0, int hi_from) {
-  const int plB = (int)((c0 >> 6) & 63), half = (int)((c0 >> 5) & 1);
-  const int idc = ((plB & 3) == 0) + (((plB >> 2) & 3) == 0) + (((plB >> 4) & 3) == 0);
+__host__ __device__ inline bool planes_hi_needed(int64_t c0, int hi_from, int letters = 6) {
+  int idc = 0;
+  for (int q = 3; q < letters; ++q) idc += ((c0 >> (2 * q)) & 3) == 0;
+  const int half = (int)((c0 >> 5) & 1);
   return idc + (half ? 2 : 3) >= hi_from;
 }
 
@@ -237,6 +241,15 @@ __device__ __forceinline__ void load_div_tables(const GenParams &P, DivTables &t
 // shots, with the exact T_i = S_i 3^(n-k) when requested) / the weighted sum
 // / 3^k (M_FINAL_W).  tab: the divisor tables in shared memory, or nullptr to
 // read them from P.
+// Index in theta of column i of the last pass (pl * C + c): unchanged, or
+// with the seven-qubit first pass (top7) qubit n's letter moved from letter 6
+// of c to the top and the letters above it (qubits 7..n-1) one down.  Runs of
+// 4096 consecutive columns stay consecutive.
+__device__ __forceinline__ int64_t theta_index(const GenParams &P, int64_t i) {
+  if (!P.top7) return i;
+  return (((i >> 12) & 3) << (2 * (P.n - 1))) | ((i >> 14) << 12) | (i & 4095);
+}
+
 template <int J, typename AccT, int MODE>
 __device__ __forceinline__ void fold_emit(const GenParams &P, const AccT (&acc)[1 << (2 * J)], int64_t ahoh,
                                           int64_t c, const DivTables *tab = nullptr) {
@@ -249,12 +262,12 @@ __device__ __forceinline__ void fold_emit(const GenParams &P, const AccT (&acc)[
   } else if constexpr (MODE == M_PARITY) {
     int64_t *out = static_cast<int64_t *>(P.out);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) out[obase + p * P.C] = (int64_t)acc[p];
+    for (int p = 0; p < NP; ++p) out[theta_index(P, obase + p * P.C)] = (int64_t)acc[p];
   } else {
     double *out = static_cast<double *>(P.out);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const int64_t i = obase + p * P.C;  // ahoh == 0 in the last pass
+      const int64_t i = theta_index(P, obase + p * P.C);  // ahoh == 0 in the last pass
       const int k = identity_letters((uint64_t)i, P.n);
       if constexpr (MODE == M_FINAL_U) {
         if (i == 0 && (int64_t)acc[p] != P.total) latch(P.status, LRE_ERR_SHOTS_MISMATCH);

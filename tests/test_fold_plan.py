@@ -45,8 +45,9 @@ def fits32(t, bound):
 
 CASES = [c for c in itertools.product(range(1, 15), (I32, I16), (0, 1), (0, 1),
                                       (0, 1, 44, 1000, 2047, 100000, 2 ** 31 // 3 ** 6, 2 ** 31 // 3 ** 6 + 1),
-                                      (0, 1), (0, 1, 2))
+                                      (0, 1), (0, 1, 2, 256, 258))
          if not (c[2] and c[3])]  # parity sums are unweighted
+RAW_TENSOR = 256  # variant flag: the raw tensor-core first pass runs (seven qubits may be folded)
 
 
 def test_every_schedule_is_exact_and_complete(plan_fn):
@@ -62,7 +63,7 @@ def test_every_schedule_is_exact_and_complete(plan_fn):
             if p["fused9"]:
                 assert k == 0 and p["J"] == 9 and p["first6"], where
             elif p["first6"]:
-                assert k == 0 and p["J"] == 6, where
+                assert k == 0 and p["J"] in (6, 7), where
             else:
                 assert 1 <= p["J"] <= (2 if weighted else 3), where
             # partial-sum type: FP64 when weighted; otherwise int32 exactly
@@ -85,10 +86,25 @@ def test_first_pass_choice(plan_fn):
     for n, kind, weighted, parity, bound, aligned, variant in CASES:
         p = plan_fn(n, kind, weighted, parity, bound, aligned, variant)[0]
         where = (n, kind, weighted, parity, bound, aligned, variant)
-        fused = not weighted and n > 9 and aligned and fits32(9, bound) and variant >= 2
-        six = not weighted and n > 6 and aligned and fits32(6, bound) and not fused
+        fused = not weighted and n > 9 and aligned and fits32(9, bound) and (variant & 255) >= 2
+        seven = (bool(variant & RAW_TENSOR) and kind == I16 and not weighted and n > 7 and aligned
+                 and fits32(7, bound) and not fused)
+        six = not weighted and n > 6 and aligned and fits32(6, bound) and not fused and not seven
         assert bool(p["fused9"]) == fused, where
-        assert bool(p["first6"]) == (fused or six), where
+        assert bool(p["first6"]) == (fused or seven or six), where
+        assert p["J"] == (9 if fused else 7 if seven else 6 if six else p["J"]), where
+
+
+def test_seven_qubit_first_pass_shrinks_every_buffer_at_n14(plan_fn):
+    # the headline shape: int16 counts, 1000 shots, the raw tensor-core pass
+    p6 = plan_fn(14, I16, 0, 0, 1000, 1, 0)
+    p7 = plan_fn(14, I16, 0, 0, 1000, 1, RAW_TENSOR)
+    assert [p["J"] for p in p6] == [6, 3, 3, 2]
+    assert [p["J"] for p in p7] == [7, 3, 3, 1]
+    assert p7[0]["out_bytes"] == 6 ** 7 * 4 ** 7 * 4
+    # each stored intermediate is two thirds of the six-qubit schedule's
+    for a, b in zip(p6[:-1], p7[:-1]):
+        assert 3 * b["out_bytes"] == 2 * a["out_bytes"]
 
 
 def test_out_of_range_n(plan_fn):

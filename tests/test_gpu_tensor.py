@@ -1,7 +1,8 @@
 """Tensor-core form of the first fold pass (tcgen05.mma kind::f16, exact
 small integers, FP32 accumulation in TMEM): bit-identical to the FWHT path
 and to the oracle, for both operand encodings (raw counts read as fp16 bit
-patterns, and fp16(1024 + c))."""
+patterns, and fp16(1024 + c)), and the raw pass folding seven qubits
+bit-identical to the six-qubit one."""
 import ctypes
 
 import numpy as np
@@ -41,7 +42,7 @@ def _sums_by_path(torch, c, n, bound, biased=0):
             lre.lre_parity_sums(ctx, c, n, S, row_total_bound=bound)
             lre.lre_sync(ctx)
             names = [k for k, _ in lre.lre_profile_records(ctx)]
-            assert any(k.startswith("fold_first6_mma") for k in names) == tensor, names
+            assert any(k.startswith(("fold_first6_mma", "fold_first7_mma")) for k in names) == tensor, names
             res.append(S)
         finally:
             lre.lre_destroy(ctx)
@@ -171,3 +172,110 @@ def test_fused_first_and_second_pass_equals_unfused(n, consumers, discard):
         finally:
             lre.lre_destroy(ctx)
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def _set_first7(lre, ctx, on):
+    f = lre.load().lre_debug_set_first7
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_int
+    assert f(ctx, on) == 0
+
+
+def _set_generic_tma(lre, ctx, on):
+    f = lre.load().lre_debug_set_generic_tma
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    f.restype = ctypes.c_int
+    assert f(ctx, on) == 0
+
+
+def _sums_six_seven(torch, c, n, bound, generic_tma=1):
+    """Parity sums with the seven-qubit raw first pass, then the six-qubit
+    one, each in a context of its own, outputs pre-filled."""
+    res = []
+    for on in (1, 0):
+        lre, ctx = ctx_and_lre()
+        try:
+            _set_first7(lre, ctx, on)
+            _set_generic_tma(lre, ctx, generic_tma)
+            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+            S = torch.full((4 ** n,), -1, dtype=torch.int64, device="cuda")
+            lre.lre_profile(ctx, True)
+            lre.lre_parity_sums(ctx, c, n, S, row_total_bound=bound)
+            lre.lre_sync(ctx)
+            names = [k for k, _ in lre.lre_profile_records(ctx)]
+            assert ("fold_first7_mma" in names) == bool(on), names
+            assert ("fold_first6_mma" in names) == (not on), names
+            res.append(S)
+        finally:
+            lre.lre_destroy(ctx)
+    return res
+
+
+# 8 = 7+1 and 9 = 7+2 (int32 partials: the next pass is the last), 10 = 7+3,
+# 11 = 7+3+1, 12 = 7+3+2 and 13 = 7+3+3 (split-plane partials)
+@pytest.mark.parametrize("n", [8, 9, 10, 11, 12, 13])
+def test_seven_qubit_first_pass_equals_six(n):
+    torch = need_gpu()
+    c = _counts(torch, n, 1000, 700 + n)
+    a, b = _sums_six_seven(torch, c, n, 1000)
+    assert torch.equal(a, b)
+    assert int(a[0]) == 1000 * 3 ** n
+
+
+def test_seven_qubit_int32_partials_equal_six():
+    """Without the TMA-staged second pass the seven-qubit pass writes int32
+    partials instead of split planes."""
+    torch = need_gpu()
+    n = 11
+    c = _counts(torch, n, 1000, 811)
+    a, b = _sums_six_seven(torch, c, n, 1000, generic_tma=0)
+    assert torch.equal(a, b)
+
+
+# shots around the seven-qubit partial sizes: 2187 x 14 fits int16 and 2187 x
+# 15 does not (the all-identity partial), 729 x 44 / 45 the same for six
+# identities, 2047 the largest raw count (2187 x 2047 < 2^23).
+@pytest.mark.parametrize("shots", [14, 15, 44, 45, 2047])
+def test_seven_qubit_split_planes_at_bound_partials(shots):
+    """Three whole tile rows (one supertile row, 3 x 729 bases) with every
+    shot in outcome 0, three more with every shot in the all-ones outcome:
+    the partials of seven qubits reach +-3^k N."""
+    torch = need_gpu()
+    n = 11
+    c = _counts(torch, n, shots, 900 + shots)
+    c[0:2187] = 0
+    c[0:2187, 0] = shots
+    c[2187:4374] = 0
+    c[2187:4374, 2 ** n - 1] = shots
+    a, b = _sums_six_seven(torch, c, n, shots)
+    assert torch.equal(a, b)
+    fwht = _sums_by_path(torch, c, n, shots)[1]
+    assert torch.equal(a, fwht)
+
+
+@pytest.mark.parametrize("n", [8, 9])
+def test_seven_qubit_theta_matches_oracle(n):
+    """theta through the seven-qubit pass against the oracle's direct sums,
+    counts up to the largest raw count with full-weight rows."""
+    torch = need_gpu()
+    lre, ctx = ctx_and_lre()
+    try:
+        lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR)
+        _set_first7(lre, ctx, 1)
+        top = 2047
+        rng = np.random.default_rng(40 + n)
+        p = np.r_[0.5, np.full(2 ** n - 1, 0.5 / (2 ** n - 1))]
+        raw = rng.multinomial(top, p, size=3 ** n)
+        raw[::5, 0] = top
+        raw[::5, 1:] = 0
+        raw[1::11, :] = 0
+        raw[1::11, -1] = top
+        raw = raw.astype(np.int16)
+        theta = torch.full((4 ** n,), -1.0, dtype=torch.float64, device="cuda")
+        lre.lre_profile(ctx, True)
+        lre.lre_estimate(ctx, torch.from_numpy(raw).cuda(), top, n, theta)
+        lre.lre_sync(ctx)
+        assert "fold_first7_mma" in [k for k, _ in lre.lre_profile_records(ctx)]
+        np.testing.assert_array_equal(theta.cpu().numpy(), direct.estimate(raw, top, n))
+    finally:
+        lre.lre_destroy(ctx)

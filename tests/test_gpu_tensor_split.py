@@ -14,7 +14,7 @@ import pytest
 
 from oracle import direct
 from tests.gpu_util import ctx_and_lre, need_gpu, rel_fro
-from tests.test_gpu_tensor import _counts, _set_variant, _sums_by_path
+from tests.test_gpu_tensor import _counts, _set_first7, _set_variant, _sums_by_path
 
 pytestmark = pytest.mark.gpu
 
@@ -102,10 +102,11 @@ def _stratified_indices(n, rng, per_k, kmax):
     return np.array(out, dtype=np.int64)
 
 
-def _bad_estimate(torch, raw, shots, n, variant=0):
+def _bad_estimate(torch, raw, shots, n, variant=0, first7=0):
     lre, ctx = ctx_and_lre()
     try:
         _set_variant(lre, ctx, variant)
+        _set_first7(lre, ctx, first7)
         lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR_SPLIT)
         theta = torch.empty(4 ** n, dtype=torch.float64, device="cuda")
         lre.lre_estimate(ctx, torch.from_numpy(raw).cuda(), shots, n, theta)
@@ -121,16 +122,19 @@ def _bad_estimate(torch, raw, shots, n, variant=0):
         lre.lre_destroy(ctx)
 
 
-@pytest.mark.parametrize("dtype,shots,variant,bad", [
-    (np.int16, 1000, 0, 1005),    # above the shots, still inside the raw encoding
-    (np.int16, 1000, 0, 2100),    # beyond the raw encoding (would read as another value)
-    (np.int16, 1000, 0, -3),      # negative
-    (np.int16, 1000, 1, 1024),    # beyond the biased encoding
-    (np.int32, 4096, 3, 4100),    # int32 planes: above the shots
-    (np.int32, 4096, 3, 70000),   # int32 planes: far beyond
-    (np.int32, 4096, 3, -1),
+@pytest.mark.parametrize("dtype,shots,variant,bad,first7", [
+    (np.int16, 1000, 0, 1005, 0),    # above the shots, still inside the raw encoding
+    (np.int16, 1000, 0, 2100, 0),    # beyond the raw encoding (would read as another value)
+    (np.int16, 1000, 0, -3, 0),      # negative
+    (np.int16, 1000, 0, 1005, 1),    # the same three through the seven-qubit pass
+    (np.int16, 1000, 0, 2100, 1),
+    (np.int16, 1000, 0, -3, 1),
+    (np.int16, 1000, 1, 1024, 0),    # beyond the biased encoding
+    (np.int32, 4096, 3, 4100, 0),    # int32 planes: above the shots
+    (np.int32, 4096, 3, 70000, 0),   # int32 planes: far beyond
+    (np.int32, 4096, 3, -1, 0),
 ])
-def test_tensor_path_latches_count_out_of_range(dtype, shots, variant, bad):
+def test_tensor_path_latches_count_out_of_range(dtype, shots, variant, bad, first7):
     """One count outside [0, shots] while the grand total still equals
     shots * 3^n (another row gives up the difference)."""
     torch = need_gpu()
@@ -150,7 +154,7 @@ def test_tensor_path_latches_count_out_of_range(dtype, shots, variant, bad):
                 delta -= t
             b += 1
     assert raw.sum() == shots * 3 ** n
-    _bad_estimate(torch, raw.astype(dtype), shots, n, variant if variant != 3 else 0)
+    _bad_estimate(torch, raw.astype(dtype), shots, n, variant if variant != 3 else 0, first7)
 
 
 @pytest.mark.parametrize("dtype,shots", [(np.int16, 1000), (np.int32, 4096)])
@@ -188,7 +192,9 @@ def test_split_planes_refuse_a_row_above_its_shots():
     times its shots (every count still within [0, shots], the grand total
     kept by emptying other rows) gives the letter I I I X X X a partial of
     42000 in a run without high planes: the tensor path latches
-    LRE_ERR_SHOTS_MISMATCH instead of returning a wrong theta."""
+    LRE_ERR_SHOTS_MISMATCH instead of returning a wrong theta.  (The
+    six-qubit first pass: at n = 10 the seven-qubit one would leave int32
+    partials, which hold any value.)"""
     torch = need_gpu()
     n, shots = 10, 1000
     raw = np.zeros((3 ** n, 2 ** n), dtype=np.int64)
@@ -200,4 +206,44 @@ def test_split_planes_refuse_a_row_above_its_shots():
     excess = int(raw[0].sum()) - shots
     raw[3 ** n - 1 - np.arange(excess // shots), 0] = 0  # the total stays shots * 3^n
     assert raw.sum() == shots * 3 ** n and raw.max() <= shots
-    _bad_estimate(torch, raw.astype(np.int16), shots, n, 0)
+    _bad_estimate(torch, raw.astype(np.int16), shots, n, 0, first7=0)
+
+
+def test_seven_qubit_planes_refuse_a_row_above_its_shots():
+    """The same row at n = 11 (7 + 3 + 1 qubits: split-plane partials of
+    seven letters).  Its tile gives the letter X I I I X X X (qubit 7 on X,
+    tile rows of axis X minus those of outcome 1) the partial 42000 in a run
+    without high planes: the seven-qubit pass latches LRE_ERR_SHOTS_MISMATCH;
+    the same context then matches the FWHT path on valid counts."""
+    torch = need_gpu()
+    n, shots = 11, 1000
+    c = torch.zeros((3 ** n, 2 ** n), dtype=torch.int16, device="cuda")
+    c[:, 0] = shots
+    o = np.arange(64)
+    even = np.array([bin((x >> 3) & 7).count("1") % 2 == 0 for x in o])
+    c[0, :] = 0
+    c[0, torch.from_numpy(o[even]).cuda()] = 500
+    excess = 500 * int(even.sum()) - shots
+    c[3 ** n - excess // shots:, 0] = 0  # the total stays shots * 3^n
+    assert int(c.sum(dtype=torch.int64)) == shots * 3 ** n
+    good = _counts(torch, n, shots, 1111)
+    theta = {}
+    for tensor in (True, False):
+        lre, ctx = ctx_and_lre()
+        try:
+            lre.lre_set_fold_path(ctx, lre.LRE_FOLD_TENSOR if tensor else lre.LRE_FOLD_FWHT)
+            _set_first7(lre, ctx, 1 if tensor else 0)
+            t = torch.full((4 ** n,), -1.0, dtype=torch.float64, device="cuda")
+            if tensor:
+                lre.lre_profile(ctx, True)
+                lre.lre_estimate(ctx, c, shots, n, t)
+                with pytest.raises(lre.LreError) as e:
+                    lre.lre_sync(ctx)
+                assert e.value.status == lre.LRE_ERR_SHOTS_MISMATCH
+                assert "fold_first7_mma" in [k for k, _ in lre.lre_profile_records(ctx)]
+            lre.lre_estimate(ctx, good, shots, n, t)
+            lre.lre_sync(ctx)
+            theta[tensor] = t
+        finally:
+            lre.lre_destroy(ctx)
+    assert torch.equal(theta[True], theta[False])
